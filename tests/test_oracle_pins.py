@@ -1,0 +1,300 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula and compares it with itself: each
+check goes through a different route (brute force, a closed form, a textbook
+identity, a published known-answer vector, a printed worked example, an
+invariant proved in the paper).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.stats as st
+
+from oracle import krr_oracle as O
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _pts(n, d, seed, scale=1.0):
+    return np.random.Generator(np.random.PCG64(seed)).uniform(0, scale, size=(n, d))
+
+
+# -------------------------------------------------------------- kernel matrix
+def test_kernel_matrix_symmetric_unit_diag_psd():
+    X = _pts(120, 3, 1)
+    K = O.kernel_matrix(X, X, 0.3)
+    assert np.array_equal(K, K.T)
+    assert np.all(np.diag(K) == 1.0)
+    lam = np.linalg.eigvalsh(K)
+    assert lam.min() >= -120 * np.finfo(float).eps * lam.max()
+
+
+def test_kernel_two_points_closed_form():
+    # K = [[1, e^{-delta^2/(2 sigma^2)}], [., 1]] for two points at distance delta
+    X = np.array([[0.0, 0.0], [0.3, 0.4]])          # delta = 0.5
+    K = O.kernel_matrix(X, X, 0.25)
+    assert K[0, 1] == pytest.approx(math.exp(-0.25 / (2 * 0.0625)), rel=1e-15)
+
+
+def test_kernel_translation_invariant():
+    X = _pts(50, 4, 2)
+    sh = np.array([3.0, -7.0, 11.0, 0.5])
+    np.testing.assert_allclose(O.kernel_matrix(X, X, 0.7), O.kernel_matrix(X + sh, X + sh, 0.7),
+                               rtol=0, atol=1e-13)
+
+
+def test_h_convention_matches_paper_gauss_transform():
+    # paper: exp(-||x-y||^2/h^2) with h = sqrt(2) sigma
+    x, y, sigma = np.array([[0.1, 0.2]]), np.array([[0.5, -0.3]]), 0.4
+    h = math.sqrt(2) * sigma
+    assert O.kernel_matrix(x, y, sigma)[0, 0] == pytest.approx(
+        math.exp(-((0.4) ** 2 + 0.5 ** 2) / h ** 2), rel=1e-15)
+
+
+def test_kmvm_brute_force_loops():
+    rng = np.random.Generator(np.random.PCG64(3))
+    X = rng.normal(size=(7, 3))
+    V = rng.normal(size=(7, 2))
+    sigma, beta = 0.9, 0.25
+    ref = np.zeros((7, 2))
+    for i in range(7):
+        for j in range(7):
+            dd = sum((X[i, c] - X[j, c]) ** 2 for c in range(3))
+            for r in range(2):
+                ref[i, r] += math.exp(-dd / (2 * sigma * sigma)) * V[j, r]
+        ref[i] += beta * V[i]
+    np.testing.assert_allclose(O.kmvm(X, V, sigma, beta), ref, rtol=1e-14, atol=1e-14)
+    rows = np.array([5, 0, 3])
+    np.testing.assert_allclose(O.kmvm(X, V, sigma, beta, rows=rows), ref[rows], rtol=1e-14)
+
+
+def test_kmvm_rect_brute_force():
+    rng = np.random.Generator(np.random.PCG64(4))
+    A, B, v = rng.normal(size=(5, 2)), rng.normal(size=(9, 2)), rng.normal(size=9)
+    ref = [sum(math.exp(-((A[i] - B[j]) ** 2).sum() / 2.0) * v[j] for j in range(9)) for i in range(5)]
+    np.testing.assert_allclose(O.kmvm_rect(A, B, v, 1.0), ref, rtol=1e-14)
+
+
+# ----------------------------------------------------------------- solve
+def test_solve_dense_residual_and_limits():
+    p = synth.small(n=300)
+    a = O.solve_dense(p.X, p.Y, p.sigma, p.beta)
+    r = O.residual(p.X, a, p.Y, p.sigma, p.beta)
+    assert np.linalg.norm(r) / np.linalg.norm(p.Y) < 1e-12
+    # beta -> infinity: alpha -> y / beta
+    big = 1e9
+    a2 = O.solve_dense(p.X, p.Y, p.sigma, big)
+    np.testing.assert_allclose(a2 * big, p.Y.astype(float), rtol=1e-5, atol=1e-6)
+    # one point: alpha = y / (1 + beta)
+    a1 = O.solve_dense(np.zeros((1, 2)), np.array([3.0]), 1.0, 0.5)
+    assert a1[0] == pytest.approx(2.0, rel=1e-15)
+
+
+def test_predict_at_training_points_is_y_minus_beta_alpha():
+    # (K + beta I) alpha = y  =>  f(x_i) = (K alpha)_i = y_i - beta alpha_i
+    p = synth.small(n=250)
+    a = O.solve_dense(p.X, p.Y[:, 0], p.sigma, p.beta)
+    f = O.predict(p.X, p.X, a, p.sigma)
+    np.testing.assert_allclose(f, p.Y[:, 0] - p.beta * a, rtol=0, atol=1e-9)
+
+
+# ------------------------------------------------------------ random matrix
+def test_philox_known_answer_vectors():
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = O.philox4x32_10(*v[0:4], v[4], v[5])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_omega_counter_layout():
+    # entry (0,0) with seed 0 is Box-Muller of the first two words of Philox(0; 0)
+    r0, r1 = 0x6627e8d5, 0xe169c58d
+    u1 = ((r0 >> 8) + 1) / 2 ** 24
+    u2 = (r1 >> 8) / 2 ** 24
+    om = O.omega(0, 3, 2)
+    assert om[0, 0] == pytest.approx(math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2), rel=1e-14)
+    assert om[1, 0] == pytest.approx(math.sqrt(-2 * math.log(u1)) * math.sin(2 * math.pi * u2), rel=1e-14)
+    # the second column uses counter word 0 = 1
+    w = O.philox4x32_10(1, 0, 0, 0, 0, 0)
+    u1 = ((int(w[0]) >> 8) + 1) / 2 ** 24
+    u2 = (int(w[1]) >> 8) / 2 ** 24
+    assert om[0, 1] == pytest.approx(math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2), rel=1e-14)
+
+
+def test_omega_is_standard_normal():
+    om = O.omega(12345, 8, 20000)
+    flat = om.ravel()
+    assert abs(flat.mean()) < 0.02
+    assert abs(flat.var() - 1.0) < 0.02
+    assert st.kstest(flat, "norm").pvalue > 1e-3
+    C = np.corrcoef(om)
+    assert np.abs(C - np.eye(8)).max() < 0.05
+    assert not np.array_equal(O.omega(1, 2, 10), O.omega(2, 2, 10))
+
+
+# --------------------------------------------------------------- pivoted QR
+def test_qrcp_matches_greedy_rule():
+    rng = np.random.Generator(np.random.PCG64(7))
+    A = rng.normal(size=(12, 60)) * rng.uniform(0.1, 3, size=60)
+    p_lapack, rd = O.qrcp(A, 10)
+    p_greedy, nrm, gap = O.qrcp_greedy(A, 10)
+    upto = np.argmax(gap < 1e-8) if np.any(gap < 1e-8) else len(gap)
+    assert upto >= 5
+    assert np.array_equal(p_lapack[:upto], p_greedy[:upto])
+    np.testing.assert_allclose(rd[:upto], nrm[:upto], rtol=1e-10)
+
+
+def test_qrcp_picks_largest_then_orthogonal():
+    # columns e1*5, e1*4 (parallel to the first), e2*3: pivots 0 then 2
+    A = np.array([[5.0, 4.0, 0.0], [0.0, 0.0, 3.0]])
+    p, rd = O.qrcp(A, 2)
+    assert list(p) == [0, 2]
+    np.testing.assert_allclose(rd, [5.0, 3.0])
+
+
+# ------------------------------------------------------ Nystrom / Woodbury
+def _nys_case(n=160, k=20, seed=5):
+    X = _pts(n, 2, seed)
+    S = O.anchor_selection(X, 0.3, k, k + 5, seed=11)
+    return X, S, O.Nystrom(X, S, 0.3, 1e-2)
+
+
+def test_woodbury_apply_equals_dense_inverse():
+    X, S, M = _nys_case()
+    K = O.kernel_matrix(X, X, 0.3)
+    C = K[:, S]
+    Kt = C @ np.linalg.pinv(K[np.ix_(S, S)], rcond=1e-13) @ C.T   # independent route
+    x = np.random.Generator(np.random.PCG64(1)).normal(size=len(X))
+    ref = np.linalg.solve(Kt + 1e-2 * np.eye(len(X)), x)
+    np.testing.assert_allclose(M.apply(x), ref, rtol=1e-8, atol=1e-8 * np.abs(ref).max())
+
+
+def test_nystrom_schur_and_spectrum_bounds():
+    X, S, M = _nys_case()
+    K = O.kernel_matrix(X, X, 0.3)
+    Kt = M.ktilde()
+    E = K - Kt
+    lam = np.linalg.eigvalsh((E + E.T) / 2)
+    assert lam.min() > -1e-10                    # Lemma schur: K - K~ >= 0
+    nrmE = lam.max()
+    mu = O.preconditioned_spectrum(K, Kt, 1e-2)  # Theorem maintheorem proof
+    assert mu.min() > 1 - 1e-8
+    assert mu.max() < 1 + nrmE / 1e-2 + 1e-6
+    lk1 = np.linalg.eigvalsh(K)[::-1][len(S)]
+    assert mu.max() / mu.min() <= O.cond_bound_id(lk1, len(S), len(X), 1e-2)
+
+
+def test_all_points_as_anchors_gives_exact_inverse():
+    X = _pts(40, 2, 9)
+    M = O.Nystrom(X, np.arange(40), 0.2, 0.05)
+    A = O.kernel_matrix(X, X, 0.2) + 0.05 * np.eye(40)
+    x = np.arange(40.0)
+    np.testing.assert_allclose(A @ M.apply(x), x, rtol=1e-6, atol=1e-6)
+
+
+def test_rank_deficient_data_converges_in_one_step():
+    # n points at only k distinct locations: rank(K) = k, K~ = K, PCG converges at once
+    base = _pts(6, 2, 3)
+    X = np.repeat(base, 10, axis=0)
+    y = np.random.Generator(np.random.PCG64(2)).normal(size=60)
+    a, it, S, M = O.solve_krr(X, y, 0.4, 0.1, k=6, seed=4, tol=1e-10)
+    assert len(set(map(tuple, X[S]))) == 6
+    assert it <= 2
+    np.testing.assert_allclose(a, O.solve_dense(X, y, 0.4, 0.1), rtol=1e-8, atol=1e-9)
+
+
+def test_svd_preconditioner_condition_number_remark():
+    # best rank-k approximation => cond = 1 + lambda_{k+1}/beta exactly (Section 4 remark)
+    X = _pts(90, 2, 8)
+    K = O.kernel_matrix(X, X, 0.25)
+    lam, V = np.linalg.eigh(K)
+    lam, V = lam[::-1], V[:, ::-1]
+    k, beta = 12, 0.03
+    Kk = (V[:, :k] * lam[:k]) @ V[:, :k].T
+    mu = O.preconditioned_spectrum(K, Kk, beta)
+    assert mu.max() / mu.min() == pytest.approx(1 + lam[k] / beta, rel=1e-8)
+
+
+# ------------------------------------------------------------------- PCG
+def test_pcg_equals_dense_cholesky():
+    p = synth.small(n=400, k=40)
+    y = p.Y[:, 0].astype(float)
+    a, it, S, M = O.solve_krr(p.X, y, p.sigma, p.beta, p.k, seed=7, tol=1e-12)
+    ref = O.solve_dense(p.X, y, p.sigma, p.beta)
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < 1e-8
+    # and the preconditioner helps: plain CG needs more iterations
+    A = O.kernel_matrix(p.X, p.X, p.sigma) + p.beta * np.eye(p.n)
+    _, it0 = O.pcg(lambda v: A @ v, y, None, tol=1e-12)
+    assert it < it0
+
+
+def test_pcg_textbook_on_spd_matrix():
+    rng = np.random.Generator(np.random.PCG64(0))
+    B = rng.normal(size=(30, 30))
+    A = B @ B.T + 30 * np.eye(30)
+    b = rng.normal(size=30)
+    x, it = O.pcg(lambda v: A @ v, b, tol=1e-13)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-10)
+    assert it <= 30 + 5
+
+
+# --------------------------------------------------------------- gradient
+def test_gradient_matches_central_differences():
+    rng = np.random.Generator(np.random.PCG64(21))
+    n, m, d = 150, 40, 3
+    X, Xv = rng.normal(size=(n, d)), rng.normal(size=(m, d))
+    y, yv = np.sin(X.sum(1)), np.sin(Xv.sum(1))
+    sigma, beta = 1.3, 0.05
+    L, gs, gb, gy = O.grad_val_mse(X, y, Xv, yv, sigma, beta)
+    assert L == pytest.approx(O.val_mse(X, y, Xv, yv, sigma, beta), rel=1e-12)
+    h = 1e-4
+    fd_s = (O.val_mse(X, y, Xv, yv, sigma * math.exp(h), beta)
+            - O.val_mse(X, y, Xv, yv, sigma * math.exp(-h), beta)) / (2 * h)
+    fd_b = (O.val_mse(X, y, Xv, yv, sigma, beta * math.exp(h))
+            - O.val_mse(X, y, Xv, yv, sigma, beta * math.exp(-h))) / (2 * h)
+    u = synth.rademacher_unit(n, 5)
+    fd_y = (O.val_mse(X, y + h * u, Xv, yv, sigma, beta)
+            - O.val_mse(X, y - h * u, Xv, yv, sigma, beta)) / (2 * h)
+    assert gs == pytest.approx(fd_s, rel=1e-6)
+    assert gb == pytest.approx(fd_b, rel=1e-6)
+    assert gy @ u == pytest.approx(fd_y, rel=1e-6)
+
+
+# ------------------------------------------------------------- theory helpers
+def test_corollary_worked_examples():
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "tradeoff_examples.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    for kind, h, n, beta, xi, d, q, exp in rows:
+        h, n, beta, xi, d, q = float(h), float(n), float(beta), float(xi), int(d), float(q)
+        if kind == "gamma":
+            # the remark prints gamma to two decimals, truncated (3.346 -> 3.34)
+            g = O.tradeoff_gamma(h, n, beta, xi, Mbar=n)
+            assert 0.0 <= g - float(exp) < 0.01
+        else:
+            assert O.tradeoff_rank([q] * d, h, n, beta, xi, Mbar=n) == eval(exp)
+
+
+def test_numerical_rank_helper_matches_corollary_proof():
+    # Eq. condbound_gamma: with delta = beta (xi - 1) / (Mbar n) (taking ||K|| = n), the
+    # theorem's gamma equals the corollary's, so the two rank formulas agree.
+    # (The theorem's bound is used as a formula only: on measured kernels it can be
+    # exceeded, e.g. 63 > 49 for 600 points in [0,2]^2, h = 0.707, delta = 1e-6.)
+    h, n, beta, xi, Mbar = 0.9, 1e5, 1e-3, 10.0, 1e5
+    delta = beta * (xi - 1) / (Mbar * n)
+    for q in ([1.0, 2.0], [0.5, 0.5, 3.0]):
+        assert O.numerical_rank_bound(q, h, delta) == O.tradeoff_rank(q, h, n, beta, xi, Mbar)
+
+
+def test_iteration_estimates_are_consistent():
+    # Eq. precond_rate2 with M lambda -> large recovers the unpreconditioned estimate's order
+    e1 = O.iters_unpreconditioned(1e4, 1e-2, 1e-6)
+    e2 = O.iters_preconditioned(1.0, 1e4, 1e-2, 1e-6)
+    assert e2 == pytest.approx(e1, rel=0.05)
+    assert O.iters_preconditioned(1.0, 1e-3, 1e-2, 1e-6) < e2
