@@ -1,0 +1,330 @@
+"""Benchmark: preconditioned Gaussian KRR solve on one GB300 (or N independent replicas).
+
+One step = the whole hot path on the resident workload: preconditioner build
+(Gaussian sketch, pivoted QR anchors, Nystrom factor, Cholesky; Algorithms 1 and 3)
+plus the refined PCG solve to a 1e-6 relative residual (Algorithm 5).  The default
+workload is the 10-component Gaussian mixture, n = 100000, d = 8, sigma = 1,
+beta = 1e-3, k = 1000 (synthetic, seeded).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "mixture"
+METRIC = "KRR solve seconds to 1e-6 rel. residual; kernel-MVM pairs/s vs roofline"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _workload(n: int | None, rank: int):
+    import synth
+    kw = {} if n is None else {"n": n}
+    return synth.mixture(seed=1000 + rank, **kw)
+
+
+def _describe(p) -> str:
+    return (f"gaussian-mixture n={p.n} d={p.d} sigma={p.sigma:g} beta={p.beta:g} k={p.k} "
+            f"l={p.l} nrhs={p.nrhs} tol={p.tol:g}")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int | None):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if self.idx is not None:
+            mine = [r for r in rows if r[0] == str(self.idx)]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _gpu_index(local_rank: int):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = vis.split(",")
+        if local_rank < len(parts) and parts[local_rank].strip().isdigit():
+            return int(parts[local_rank])
+        return None
+    return local_rank
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(p, mvm_count: int, budget_s: float = 15.0) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload's rows and scale it to
+    one solve: n rows x (one sketch row with l columns + mvm_count product rows)."""
+    from oracle import krr_oracle as O
+    rng = np.random.Generator(np.random.PCG64(7))
+    X64 = p.X.astype(np.float64)
+    y64 = p.Y.astype(np.float64)
+    Om = O.omega(11, p.l, p.n).T.copy()
+    t_row_mvm = t_row_sk = None
+    rows_done = 0
+    t0 = time.perf_counter()
+    nrows = 8
+    while True:
+        rows = rng.choice(p.n, nrows, replace=False)
+        a = time.perf_counter()
+        O.kmvm(X64, y64, p.sigma, p.beta, rows=rows)
+        b = time.perf_counter()
+        O.kmvm_rect(X64[rows], X64, Om, p.sigma)
+        c = time.perf_counter()
+        t_row_mvm = (b - a) / nrows
+        t_row_sk = (c - b) / nrows
+        rows_done += nrows
+        if time.perf_counter() - t0 > budget_s / 3 or nrows >= 256:
+            break
+        nrows *= 2
+    est = p.n * (t_row_sk + mvm_count * t_row_mvm)
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"{rows_done} rows of the FP64 oracle product (1 RHS) and of the sketch "
+                       f"(l={p.l} columns) at n={p.n}; scaled to n rows x ({mvm_count} products + "
+                       f"1 sketch); pivoted QR and k x k factorisations not included"),
+            "per_row_product_s": t_row_mvm, "per_row_sketch_s": t_row_sk,
+            "elapsed_s": time.perf_counter() - t0}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = _workload(args.n, 0)
+    mvm_guess = 240   # products of a typical solve of this workload on the GPU path
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(p, mvm_guess, budget_s=min(20.0, 120.0 / max(1, args.warmup + args.steps)))
+        if s >= args.warmup:
+            vals.append(r)
+    v = float(np.mean([r["value"] for r in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _describe(p), "l2": "n/a (host)"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_1905_10587_gb300.build import build
+    if rank == 0:
+        build()
+    if dist:
+        dist.barrier()
+    build()
+    from paper_1905_10587_gb300 import api
+
+    p = _workload(args.n, rank)
+    X = torch.from_numpy(p.X).to(dev)
+    Y = torch.from_numpy(p.Y).to(dev)
+    ctx = api.KRR()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+
+    def step():
+        ctx.build(X, p.sigma, p.beta, p.k, seed=1)
+        return ctx.solve(Y, tol=p.tol)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ctx.profile(True)
+    sampler = ClockSampler(_gpu_index(local))
+    sampler.start()
+    launches0 = ctx.launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    total_ms = 0.0
+    infos = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)   # L2 flush between steps (outside the timed events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        alpha, info = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        infos.append(info)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = ctx.launches - launches0
+    clocks = sampler.stop()
+    phases = ctx.phase_times()
+    ctx.profile(False)
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    ms_per_step = max_ms / args.steps
+    value = ms_per_step / 1e3 / world   # seconds per solve across the whole job
+
+    # ---- dominant kernel: the tiled kernel product of the PCG iterations
+    kms, kcnt = phases["kmvm"]
+    pairs = float(p.n) * p.n * p.nrhs
+    d, nrhs = p.d, p.nrhs
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    ffma_rate = sms * 128 * sm_max          # FP32 lanes per SM x clock
+    mufu_rate = sms * 16 * sm_max           # ex2 per SM per clock x clock
+    per_pair_fma = d + 1 + nrhs             # d FFMA (dot) + FADD (norms) + nrhs FFMA
+    peak_pairs = min(ffma_rate / per_pair_fma, mufu_rate)
+    avg_s = (kms / max(kcnt, 1)) / 1e3
+    achieved = (float(p.n) * p.n / avg_s) if kcnt else None
+    roof = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
+            "peak": peak_pairs / 1e9, "unit": "Gpair/s",
+            "frac": (achieved / peak_pairs) if achieved else None, "traffic": None,
+            "kernel": "k_kmvm (tiled FP32 kernel product, (K + beta I) p)",
+            "peak_basis": (f"recipe units x max clock: {sms} SMs x 128 FP32 lanes / "
+                           f"{per_pair_fma} FMA-pipe ops per pair vs {sms} SMs x 16 ex2; "
+                           f"{sm_max / 1e6:.0f} MHz"),
+            "launches": kcnt, "avg_launch_ms": avg_s * 1e3}
+
+    out = None
+    if rank == 0:
+        last = infos[-1]
+        out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+               "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32", "data": "synthetic",
+               "config": {"workload": _describe(p), "l2": "flushed between steps (256 MiB write)",
+                          "precision": "FP32 kernel tiles, FP64 scalars, FP64 refinement residual",
+                          "replicas": world},
+               "roofline": roof, "clocks": clocks, "gpu_launches": launches,
+               "mvm_pairs_per_s": pairs * kcnt / (kms / 1e3) if kcnt else None,
+               "solve": {"iters": last["iters"], "sweeps": last["sweeps"], "k_eff": last["k_eff"],
+                         "mvm_count": last["mvm_count"], "rel_residual": last["rel_residual"][0],
+                         "build_ms": last["build_ms"], "solve_ms": last["solve_ms"]},
+               "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]}}
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        Xh = torch.from_numpy(p.X).pin_memory()
+        Yh = torch.from_numpy(p.Y[:, 0].copy()).pin_memory()
+        e2e_ms = 0.0
+        for s in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a, _ = api.solve(Xh, Yh, p.sigma, p.beta, p.k, seed=1, tol=p.tol)
+            e1.record()
+            e1.synchronize()
+            if s:
+                e2e_ms += e0.elapsed_time(e1)
+        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        if out is not None:
+            out["e2e"] = {"value": float(te.item()) / args.e2e_steps / 1e3 / world, "unit": "s",
+                          "h2d_bytes_per_step": int(Xh.numel() * 4 + Yh.numel() * 4),
+                          "d2h_bytes_per_step": int(p.n * 8)}
+
+    if out is not None:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_sample(p, out["solve"]["mvm_count"])
+        try:
+            peaks = {}
+            for kind, name in ((0, "ffma_per_s"), (1, "ex2_per_s"), (2, "dfma_per_s")):
+                peaks[name] = api.peak_probe(kind)
+            out["probe_peaks"] = peaks
+        except Exception as e:  # pragma: no cover
+            out["probe_peaks"] = {"error": str(e)}
+        print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller test runs)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

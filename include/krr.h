@@ -1,0 +1,181 @@
+/*
+ * krr.h - C ABI of the GB300 (sm_103a) Gaussian kernel ridge regression solver.
+ *
+ * The solver computes alpha = (K + beta I)^{-1} y for the Gaussian kernel
+ *     K_ij = exp(-||x_i - x_j||^2 / (2 sigma^2))
+ * by preconditioned conjugate gradient, following Shabat, Choshen, Ben-Or and
+ * Carmel, "Fast and Accurate Gaussian Kernel Ridge Regression Using Matrix
+ * Decompositions for Preconditioning" (arXiv 1905.10587):
+ *   - the problem is Eq. (1) and Eq. (ridge_regression) of Section 1;
+ *   - the kernel product is the discrete Gauss transform (Section 2.3,
+ *     Eq. dscrt_gt), here evaluated exactly in tiles without storing K;
+ *     the paper's width h equals sqrt(2) * sigma;
+ *   - anchors come from Algorithm 1 (Gaussian sketch + pivoted QR);
+ *   - the preconditioner is Algorithm 3 (Nystrom factor + Cholesky of
+ *     Eq. chol_factor), applied by Algorithm 4 (Woodbury, Eq. woodbury);
+ *   - the driver is Algorithm 5 (PCG).
+ *
+ * Conventions (all entry points):
+ *   - Every array argument is a DEVICE pointer owned by the caller, unless
+ *     the comment says "host".  The library never frees caller memory.
+ *   - Point sets are row-major float32: X[i * d + c], i < n, c < d.
+ *   - Multi-column vectors (right-hand sides, solutions) are RHS-major:
+ *     column r of an n x nrhs block starts at ptr + r * n.
+ *   - A context owns its device workspace (allocated with cudaMalloc, grown on
+ *     demand, released by krr_destroy) and issues all work on the stream given
+ *     to krr_create.  A context is not thread-safe.
+ *   - Return value: KRR_OK or a KRR_E_* code.  Nothing aborts or throws; the
+ *     message of the last failure is available from krr_last_error().
+ *   - Preconditions are checked on the host before any launch: n >= 1,
+ *     1 <= d <= KRR_MAX_DIM, sigma > 0, beta > 0 where the method needs it,
+ *     1 <= k <= n, 1 <= nrhs <= KRR_MAX_RHS, non-null pointers.  A bad argument
+ *     returns KRR_E_INVAL and launches nothing.
+ */
+#ifndef KRR_H_
+#define KRR_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KRR_OK        0
+#define KRR_E_INVAL   1   /* bad argument (host-side check; nothing launched)        */
+#define KRR_E_CUDA    2   /* a CUDA runtime call failed                              */
+#define KRR_E_NOTSPD  3   /* an FP64 Cholesky met a pivot <= 0 even after a shift   */
+#define KRR_E_NOCONV  4   /* tolerance not reached within the iteration limits      */
+#define KRR_E_STATE   5   /* call out of order (e.g. solve before build)             */
+#define KRR_E_NOMEM   6   /* workspace allocation failed                             */
+#define KRR_E_NONFINITE 7 /* NaN or Inf met in an input or a reduction               */
+
+#define KRR_MAX_DIM  64
+#define KRR_MAX_RHS  16
+
+typedef struct krr_ctx krr_ctx;
+
+/* Solver options.  krr_default_opts() fills the defaults given here. */
+typedef struct krr_opts {
+    int    max_iter;      /* PCG iterations per refinement sweep (default 1000)          */
+    int    refine_max;    /* outer refinement sweeps (default 6)                         */
+    int    oversample;    /* l = k + oversample random projections (default 5, Sec. 5.1) */
+    int    check_every;   /* iterations between host convergence reads (default 1)      */
+    double inner_tol;     /* relative tolerance of each inner PCG solve (default 1e-4)   */
+    double anchor_rtol;   /* pivots with |R_jj| < anchor_rtol |R_11| are dropped (1e-5)  */
+    int    precision;     /* 0: FP32 kernel tiles (default); reserved for other modes   */
+    int    reserved[7];
+} krr_opts;
+
+/* Per-solve report (host struct). */
+typedef struct krr_solve_info {
+    int    status;                        /* KRR_OK or KRR_E_NOCONV                   */
+    int    iters;                         /* PCG iterations summed over sweeps        */
+    int    sweeps;                        /* refinement sweeps run                    */
+    int    k_eff;                         /* anchors kept by the build                */
+    double rel_residual[KRR_MAX_RHS];     /* ||y - (K+beta I) alpha|| / ||y||, FP64   */
+    double build_ms;                      /* time of the last krr_build_precond       */
+    double solve_ms;                      /* wall time of this solve (host clock)     */
+    int    mvm_count;                     /* kernel products (K+beta I)V issued       */
+    int    reserved[7];
+} krr_solve_info;
+
+/* Fill *opts with the defaults.  Returns KRR_E_INVAL if opts is NULL. */
+int krr_default_opts(krr_opts* opts);
+
+/* Create a context on the current CUDA device.  opts may be NULL (defaults);
+ * stream is a cudaStream_t (NULL = legacy default stream). */
+int krr_create(krr_ctx** ctx, const krr_opts* opts, void* stream);
+
+/* Release the context and all workspace it owns.  NULL is allowed. */
+void krr_destroy(krr_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none); host string owned by ctx. */
+const char* krr_last_error(const krr_ctx* ctx);
+
+/* Number of kernel launches this context has issued so far (host counter). */
+long long krr_launch_count(const krr_ctx* ctx);
+
+/* Phase timers.  krr_profile_enable(ctx, 1) clears the records and brackets each
+ * phase of later calls with CUDA events on the context's stream; krr_profile_read
+ * sums the recorded durations of one phase ("kmvm", "sketch", "omega", "qrcp",
+ * "fgemm", "gram", "chol", "apply", "resid_hp", "cgvec", "prep") and counts its
+ * occurrences (host outputs; synchronises on the recorded events). */
+int krr_profile_enable(krr_ctx* ctx, int on);
+int krr_profile_read(krr_ctx* ctx, const char* phase, double* total_ms, long long* count);
+
+/* Whole-GPU issue-rate probe used for roofline denominators: kind 0 = FP32 FFMA,
+ * 1 = MUFU ex2, 2 = FP64 DFMA.  Writes operations per second to *ops_per_s (host).
+ * Runs on the current device and the given stream (NULL = default stream). */
+int krr_peak_probe(int kind, double* ops_per_s, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Kernel products (Section 2.3, Eq. dscrt_gt; Definition figtree_def).
+ * Q = K(Xr, Xc) V + beta * V[0:nr]   (Q: nr x nrhs, V: nc x nrhs, RHS-major).
+ * K(Xr, Xc)_ij = exp(-||xr_i - xc_j||^2 / (2 sigma^2)), evaluated in FP32 tiles
+ * from the expansion ||x||^2 + ||y||^2 - 2 x.y after centring both sets on the
+ * mean of Xc; K is never stored.  beta must be 0 unless nr == nc (square
+ * product with the ridge term).  Xr may equal Xc.
+ * ------------------------------------------------------------------------- */
+int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc,
+             int d, double sigma, double beta, const float* V, int nrhs, float* Q);
+
+/* High-precision residual R = Y - (K(X, X) + beta I) A with FP64 alpha A and FP64
+ * output R (n x nrhs each, RHS-major); K entries and sums carried in FP64 from
+ * exact differences of the float32 coordinates.  Used for the refinement step. */
+int krr_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                    const float* Y, const double* A, int nrhs, double* R);
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1 pieces.
+ * ------------------------------------------------------------------------- */
+/* The Gaussian test matrix of Algorithm 1 step 1, written transposed: OmT[j*l + a]
+ * = omega_{a,j}, j < n, a < l.  Entry (a, j) is Box-Muller on Philox4x32-10
+ * (Salmon et al., SC'11) with counter (j mod 2^32, j div 2^32, a div 2, 0) and key
+ * (seed mod 2^32, seed div 2^32): u1 = ((r0 >> 8) + 1) 2^-24, u2 = (r1 >> 8) 2^-24,
+ * omega_{2c} = sqrt(-2 ln u1) cos(2 pi u2), omega_{2c+1} = sqrt(-2 ln u1) sin(2 pi u2). */
+int krr_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, float* OmT);
+
+/* Sketch Y = K(X, X) Omega^T of Algorithm 1 step 2: Y is n x l row-major
+ * (Y[i*l + a]).  Omega is generated as krr_omega describes. */
+int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, int l,
+               unsigned long long seed, float* Y);
+
+/* Column-pivoted QR pivot selection of Algorithm 1 steps 3-4 on Y^T (Y is n x l
+ * row-major, so the columns of Y^T are the rows of Y): returns the first k pivots
+ * (device int32 piv[k]) and |R_jj| (device float rdiag[k]).  Rule: the largest
+ * remaining residual norm, lowest index on ties.  Y is overwritten (residuals). */
+int krr_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int k, int* piv, float* rdiag);
+
+/* ---------------------------------------------------------------------------
+ * Algorithms 3-5.
+ * ------------------------------------------------------------------------- */
+/* Build the preconditioner (Algorithm 5 steps 1-2: Algorithm 1 then Algorithm 3)
+ * for (X, sigma, beta) with k anchors and l = k + opts.oversample projections.
+ * X must stay valid and unchanged until the last krr_solve/krr_predict on it. */
+int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double sigma,
+                      double beta, int k, unsigned long long seed);
+
+/* Build with caller-given anchors S (device int32[k], indices into X). */
+int krr_build_precond_anchors(krr_ctx* ctx, const float* X, long long n, int d, double sigma,
+                              double beta, const int* S, int k);
+
+/* Anchors kept by the last build: writes k_eff (host) and S (device int32[k_eff], may be NULL). */
+int krr_get_anchors(krr_ctx* ctx, int* S, int* k_eff);
+
+/* Out = (K~ + beta I)^{-1} In (Algorithm 4; Eq. woodbury), In/Out n x nrhs FP32. */
+int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out);
+
+/* Solve (K + beta I) alpha = Y (Algorithm 5 step 3) for the built X to
+ * ||Y - (K + beta I) alpha|| / ||Y|| <= tol per column, measured with the FP64
+ * residual.  X must be the pointer given to the build.  alpha: n x nrhs FP64.
+ * info (host) may be NULL.  Returns KRR_E_NOCONV (alpha still written) if
+ * the limits are hit first. */
+int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol,
+              double* alpha, krr_solve_info* info);
+
+/* f = K(Xtest, X) alpha (Eq. (1)); Xtest m x d, alpha n x nrhs FP32, f m x nrhs. */
+int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alpha, int nrhs,
+                float* f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRR_H_ */

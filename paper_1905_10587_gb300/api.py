@@ -1,0 +1,224 @@
+"""Thin Python binding over the C ABI (argument marshalling only).
+
+Every computation happens in libkrr's CUDA kernels; this module only checks
+shapes, makes tensors contiguous, passes device pointers and the current CUDA
+stream, and turns status codes into exceptions.  Multi-column blocks are
+exchanged as (n, nrhs) tensors and handed to the library RHS-major.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+
+class KRRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{L.STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _cuda(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return t.contiguous()
+
+
+def _cols(V: torch.Tensor, dtype: torch.dtype, name: str):
+    """(n,) or (n, nrhs) -> RHS-major contiguous (nrhs, n) and a flag for 1-D input."""
+    V = _cuda(V, dtype, name)
+    if V.dim() == 1:
+        return V.reshape(1, -1).contiguous(), True
+    if V.dim() != 2:
+        raise ValueError(f"{name} must be 1-D or 2-D")
+    return V.t().contiguous(), False
+
+
+def _uncols(Q: torch.Tensor, vec: bool) -> torch.Tensor:
+    return Q.reshape(-1) if vec else Q.t()
+
+
+class KRR:
+    """One solver context (workspace, preconditioner state) on the current device and stream."""
+
+    def __init__(self, stream: torch.cuda.Stream | None = None, **opts):
+        self.lib = L.load()
+        o = L.KrrOpts()
+        self.lib.krr_default_opts(C.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.stream = stream or torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = self.lib.krr_create(C.byref(h), C.byref(o), C.c_void_p(self.stream.cuda_stream))
+        if rc != 0:
+            raise KRRError(rc, "krr_create failed")
+        self.h = h
+        self._X = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.krr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, allow=(0,)):
+        if rc not in allow:
+            raise KRRError(rc, self.lib.krr_last_error(self.h).decode())
+        return rc
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.krr_launch_count(self.h))
+
+    def profile(self, on: bool = True):
+        self._check(self.lib.krr_profile_enable(self.h, 1 if on else 0))
+
+    PHASES = ("kmvm", "sketch", "omega", "qrcp", "fgemm", "gram", "chol", "apply", "resid_hp",
+              "cgvec", "prep")
+
+    def phase_times(self) -> dict:
+        """{phase: (total_ms, count)} of the recorded phases."""
+        out = {}
+        for ph in self.PHASES:
+            ms, cnt = C.c_double(), C.c_longlong()
+            self._check(self.lib.krr_profile_read(self.h, ph.encode(), C.byref(ms), C.byref(cnt)))
+            out[ph] = (ms.value, cnt.value)
+        return out
+
+    # ---------------------------------------------------------------- products
+    def kmvm(self, Xr, Xc, V, sigma: float, beta: float = 0.0) -> torch.Tensor:
+        """K(Xr, Xc) V + beta V (Section 2.3, Eq. dscrt_gt)."""
+        Xr = _cuda(Xr, torch.float32, "Xr")
+        Xc = _cuda(Xc, torch.float32, "Xc")
+        Vt, vec = _cols(V, torch.float32, "V")
+        Q = torch.empty((Vt.shape[0], Xr.shape[0]), device=Xr.device, dtype=torch.float32)
+        self._check(self.lib.krr_kmvm(self.h, _ptr(Xr), Xr.shape[0], _ptr(Xc), Xc.shape[0],
+                                      Xr.shape[1], sigma, beta, _ptr(Vt), Vt.shape[0], _ptr(Q)))
+        return _uncols(Q, vec)
+
+    def residual_hp(self, X, Y, A, sigma: float, beta: float) -> torch.Tensor:
+        """Y - (K + beta I) A in FP64 (A float64, Y float32)."""
+        X = _cuda(X, torch.float32, "X")
+        Yt, vec = _cols(Y, torch.float32, "Y")
+        At, _ = _cols(A, torch.float64, "A")
+        R = torch.empty_like(At)
+        self._check(self.lib.krr_residual_hp(self.h, _ptr(X), X.shape[0], X.shape[1], sigma, beta,
+                                             _ptr(Yt), _ptr(At), Yt.shape[0], _ptr(R)))
+        return _uncols(R, vec)
+
+    # ---------------------------------------------------------------- Algorithm 1
+    def omega(self, seed: int, l: int, n: int, device=None) -> torch.Tensor:
+        """Omega^T (n x l) of Algorithm 1 step 1."""
+        Om = torch.empty((n, l), device=device or torch.device("cuda"), dtype=torch.float32)
+        self._check(self.lib.krr_omega(self.h, seed, l, n, _ptr(Om)))
+        return Om
+
+    def sketch(self, X, sigma: float, l: int, seed: int) -> torch.Tensor:
+        """Y = K Omega^T (n x l) of Algorithm 1 step 2."""
+        X = _cuda(X, torch.float32, "X")
+        Y = torch.empty((X.shape[0], l), device=X.device, dtype=torch.float32)
+        self._check(self.lib.krr_sketch(self.h, _ptr(X), X.shape[0], X.shape[1], sigma, l, seed,
+                                        _ptr(Y)))
+        self._X = None
+        return Y
+
+    def qrcp(self, Y, k: int):
+        """First k pivots of the column-pivoted QR of Y^T and |R_jj| (Y is consumed)."""
+        Y = _cuda(Y, torch.float32, "Y").clone()
+        piv = torch.empty(k, device=Y.device, dtype=torch.int32)
+        rd = torch.empty(k, device=Y.device, dtype=torch.float32)
+        self._check(self.lib.krr_qrcp(self.h, _ptr(Y), Y.shape[0], Y.shape[1], k, _ptr(piv), _ptr(rd)))
+        return piv, rd
+
+    # ---------------------------------------------------------------- Algorithms 3-5
+    def build(self, X, sigma: float, beta: float, k: int, seed: int = 0, anchors=None):
+        """Algorithm 5 steps 1-2: anchors (Algorithm 1, or the given ones) and Algorithm 3."""
+        X = _cuda(X, torch.float32, "X")
+        if anchors is None:
+            rc = self.lib.krr_build_precond(self.h, _ptr(X), X.shape[0], X.shape[1], sigma, beta,
+                                            k, seed)
+        else:
+            S = _cuda(anchors, torch.int32, "anchors")
+            rc = self.lib.krr_build_precond_anchors(self.h, _ptr(X), X.shape[0], X.shape[1], sigma,
+                                                    beta, _ptr(S), S.numel())
+        self._check(rc)
+        self._X = X   # keeps the points alive: the library reads them during solves
+        return self
+
+    def anchors(self) -> torch.Tensor:
+        k = C.c_int()
+        self._check(self.lib.krr_get_anchors(self.h, None, C.byref(k)))
+        S = torch.empty(k.value, device=self._X.device, dtype=torch.int32)
+        self._check(self.lib.krr_get_anchors(self.h, _ptr(S), C.byref(k)))
+        return S
+
+    def apply_precond(self, R) -> torch.Tensor:
+        """(K~ + beta I)^{-1} R (Algorithm 4)."""
+        Rt, vec = _cols(R, torch.float32, "R")
+        Z = torch.empty_like(Rt)
+        self._check(self.lib.krr_precond_apply(self.h, _ptr(Rt), Rt.shape[0], _ptr(Z)))
+        return _uncols(Z, vec)
+
+    def solve(self, Y, tol: float = 1e-6, allow_noconv: bool = False):
+        """Algorithm 5 step 3: alpha (float64) with ||Y - (K+beta I) alpha|| / ||Y|| <= tol."""
+        if self._X is None:
+            raise KRRError(L.KRR_E_STATE, "solve before build")
+        Yt, vec = _cols(Y, torch.float32, "Y")
+        A = torch.empty(Yt.shape, device=Yt.device, dtype=torch.float64)
+        info = L.KrrSolveInfo()
+        allow = (0, L.KRR_E_NOCONV) if allow_noconv else (0,)
+        self._check(self.lib.krr_solve(self.h, _ptr(self._X), _ptr(Yt), Yt.shape[0], tol, _ptr(A),
+                                       C.byref(info)), allow)
+        out = dict(status=info.status, iters=info.iters, sweeps=info.sweeps, k_eff=info.k_eff,
+                   rel_residual=[info.rel_residual[i] for i in range(Yt.shape[0])],
+                   build_ms=info.build_ms, solve_ms=info.solve_ms, mvm_count=info.mvm_count)
+        return _uncols(A, vec), out
+
+    def predict(self, Xtest, alpha) -> torch.Tensor:
+        """f = K(Xtest, X) alpha (Eq. (1))."""
+        Xt = _cuda(Xtest, torch.float32, "Xtest")
+        At, vec = _cols(alpha.float() if alpha.dtype != torch.float32 else alpha, torch.float32, "alpha")
+        f = torch.empty((At.shape[0], Xt.shape[0]), device=Xt.device, dtype=torch.float32)
+        self._check(self.lib.krr_predict(self.h, _ptr(Xt), Xt.shape[0], _ptr(At), At.shape[0], _ptr(f)))
+        return _uncols(f, vec)
+
+
+def peak_probe(kind: int) -> float:
+    """Measured issue rate (ops/s) of the whole GPU: 0 FFMA, 1 MUFU ex2, 2 DFMA."""
+    lib = L.load()
+    v = C.c_double()
+    rc = lib.krr_peak_probe(kind, C.byref(v), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise KRRError(rc, "peak probe failed")
+    return v.value
+
+
+def solve(X, y, sigma: float, beta: float, k: int, seed: int = 0, tol: float = 1e-6, **opts):
+    """One-call solve through the public API.  X, y may live on the host: they are copied
+    to the current CUDA device, and alpha comes back on the device of the inputs."""
+    host = not X.is_cuda
+    dev = torch.device("cuda")
+    Xd = X.to(dev, non_blocking=True) if host else X
+    yd = y.to(dev, non_blocking=True) if host else y
+    ctx = KRR(**opts)
+    ctx.build(Xd, sigma, beta, k, seed)
+    alpha, info = ctx.solve(yd, tol)
+    ctx.close()
+    return (alpha.cpu() if host else alpha), info

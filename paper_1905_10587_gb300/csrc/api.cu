@@ -1,0 +1,599 @@
+// extern "C" entry points of libkrr (declared in include/krr.h) and the host-side
+// drivers: the preconditioner build (Algorithm 5 steps 1-2 = Algorithms 1 and 3)
+// and the refined PCG solve (Algorithm 5 step 3 inside FP64 iterative refinement).
+#include "internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace krr {
+
+int fail(krr_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+const char* const kPhaseNames[PH_COUNT] = {"kmvm", "sketch", "omega", "qrcp", "fgemm", "gram",
+                                           "chol", "apply", "resid_hp", "cgvec", "prep"};
+
+static cudaEvent_t pool_event(krr_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+Phase::Phase(krr_ctx* ctx, int id) : ctx_(ctx), id_(id) {
+    if (!ctx_->prof) return;
+    start_ = pool_event(ctx_);
+    if (start_) cudaEventRecord(start_, ctx_->stream);
+}
+
+Phase::~Phase() {
+    if (!ctx_->prof || !start_) return;
+    cudaEvent_t stop = pool_event(ctx_);
+    if (!stop) return;
+    cudaEventRecord(stop, ctx_->stream);
+    ctx_->prof_recs.push_back(PhaseRec{start_, stop, id_});
+}
+
+int buf(krr_ctx* ctx, const char* name, size_t bytes, void** out) {
+    Buf& b = ctx->bufs[name];
+    if (bytes == 0) bytes = 16;
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        const size_t want = (bytes + 255) / 256 * 256;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(ctx, KRR_E_NOMEM, std::string("workspace '") + name + "': " +
+                                              cudaGetErrorString(e));
+        }
+        b.bytes = want;
+    }
+    *out = b.p;
+    return KRR_OK;
+}
+
+// launchers implemented in cg.cu that only the drivers use
+int cg_vec_blocks(krr_ctx* ctx);
+int launch_cg_start(krr_ctx* ctx, const float* r, const float* z, int nrhs, double* rz_part,
+                    double* rr_part);
+int launch_cg_alpha(krr_ctx* ctx, const float* p, const float* q, int nrhs, double* part);
+int launch_cg_update_xr(krr_ctx* ctx, float* x, float* r, const float* p, const float* q, int nrhs,
+                        double* part, double tol2);
+int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const double* rz_part);
+int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot);
+int launch_convert_up(krr_ctx* ctx, const float* a, double* b, long long tot);
+int launch_accumulate(krr_ctx* ctx, const float* x, double* y, long long tot);
+
+static const double LOG2E = 1.4426950408889634;
+
+static int check_points(krr_ctx* ctx, const void* X, long long n, int d) {
+    if (!X) return fail(ctx, KRR_E_INVAL, "null point array");
+    if (n < 1) return fail(ctx, KRR_E_INVAL, "n must be >= 1");
+    if (n > 0x7fffffffLL) return fail(ctx, KRR_E_INVAL, "n must be < 2^31");
+    if (d < 1 || d > KRR_MAX_DIM) return fail(ctx, KRR_E_INVAL, "d must be in [1, 64]");
+    return KRR_OK;
+}
+
+static int check_sigma_beta(krr_ctx* ctx, double sigma, double beta, bool need_beta) {
+    if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(ctx, KRR_E_INVAL, "sigma must be > 0");
+    if (need_beta && (!(beta > 0.0) || !std::isfinite(beta)))
+        return fail(ctx, KRR_E_INVAL, "beta must be > 0");
+    if (!need_beta && (!(beta >= 0.0) || !std::isfinite(beta)))
+        return fail(ctx, KRR_E_INVAL, "beta must be >= 0");
+    return KRR_OK;
+}
+
+static double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- preconditioner build
+static int build_from_anchors(krr_ctx* ctx, const int* S_dev, int k_eff) {
+    const long long n = ctx->n;
+    const int d = ctx->d, ps = ctx->ps;
+    ctx->k_eff = k_eff;
+    KRR_RET(bufT(ctx, "S", (size_t)k_eff, &ctx->S));
+    if (S_dev != ctx->S)
+        KRR_TRY_CUDA(cudaMemcpyAsync(ctx->S, S_dev, sizeof(int) * k_eff, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    KRR_RET(bufT(ctx, "PS", (size_t)k_eff * ps, &ctx->PS));
+    KRR_RET(bufT(ctx, "XS", (size_t)k_eff * d, &ctx->XS));
+    {
+        Phase ph(ctx, PH_PREP);
+        KRR_RET(launch_gather_pack(ctx, ctx->P, ps, ctx->X, d, ctx->S, k_eff, ctx->PS, ctx->XS));
+    }
+
+    // L1 L1^T = K_SS (FP64); a tiny diagonal shift is added only if the factorisation fails
+    double *L1, *L1inv;
+    KRR_RET(bufT(ctx, "L1", (size_t)k_eff * k_eff, &L1));
+    KRR_RET(bufT(ctx, "L1inv", (size_t)k_eff * k_eff, &L1inv));
+    int info = 0;
+    double shift = 0.0;
+    {
+        Phase ph_chol(ctx, PH_CHOL);
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            KRR_RET(launch_kss(ctx, ctx->XS, k_eff, d, ctx->sigma, L1));
+            if (shift > 0.0) KRR_RET(launch_add_diag(ctx, L1, k_eff, shift));
+            KRR_RET(launch_potrf(ctx, L1, k_eff, &info));
+            if (info == 0) break;
+            shift = shift == 0.0 ? 1e-12 * k_eff : shift * 1e3;
+        }
+        if (info != 0) return fail(ctx, KRR_E_NOTSPD, "Cholesky of K_SS failed");
+        KRR_RET(launch_set_identity(ctx, L1inv, k_eff));
+        KRR_RET(launch_trsm_lower(ctx, L1, L1inv, k_eff));
+    }
+
+    // F = K(X, X_S) L1^{-T}  (n x ldF)
+    ctx->ldF = (k_eff + 3) / 4 * 4;
+    float* W32;
+    KRR_RET(bufT(ctx, "W32", (size_t)k_eff * ctx->ldF, &W32));
+    KRR_RET(launch_to_float_transposed(ctx, L1inv, k_eff, W32, ctx->ldF));
+    KRR_RET(bufT(ctx, "F", (size_t)n * ctx->ldF, &ctx->F));
+    {
+        Phase ph(ctx, PH_FGEMM);
+        KRR_TRY_CUDA(cudaMemsetAsync(ctx->F, 0, sizeof(float) * n * ctx->ldF, ctx->stream));
+        KRR_RET(launch_kgemm(ctx, ctx->P, n, ctx->PS, k_eff, d, W32, ctx->ldF, k_eff, ctx->F,
+                             ctx->ldF));
+    }
+
+    // G = beta I + F^T F = L2 L2^T;  T2 = L2^{-1}
+    double* G;
+    KRR_RET(bufT(ctx, "G", (size_t)k_eff * k_eff, &G));
+    {
+        Phase ph(ctx, PH_GRAM);
+        KRR_RET(launch_gram(ctx, ctx->F, n, k_eff, ctx->ldF, ctx->beta, G));
+    }
+    Phase ph_chol2(ctx, PH_CHOL);   // until the end of the build
+    KRR_RET(launch_potrf(ctx, G, k_eff, &info));
+    if (info != 0) return fail(ctx, KRR_E_NOTSPD, "Cholesky of beta I + F^T F failed");
+    KRR_RET(bufT(ctx, "T2", (size_t)k_eff * k_eff, &ctx->T2));
+    KRR_RET(bufT(ctx, "T2t", (size_t)k_eff * k_eff, &ctx->T2t));
+    KRR_RET(launch_set_identity(ctx, ctx->T2, k_eff));
+    KRR_RET(launch_trsm_lower(ctx, G, ctx->T2, k_eff));
+    KRR_RET(launch_transpose64(ctx, ctx->T2, ctx->T2t, k_eff));
+    return KRR_OK;
+}
+
+static int build_common(krr_ctx* ctx, const float* X, long long n, int d, double sigma,
+                        double beta) {
+    ctx->built = false;
+    ctx->X = X;
+    ctx->n = n;
+    ctx->d = d;
+    ctx->ps = packed_stride(d);
+    ctx->sigma = sigma;
+    ctx->beta = beta;
+    ctx->s = LOG2E / (2.0 * sigma * sigma);
+    double* mu;
+    KRR_RET(bufT(ctx, "mu", (size_t)d, &mu));
+    KRR_RET(bufT(ctx, "P", (size_t)n * ctx->ps, &ctx->P));
+    Phase ph(ctx, PH_PREP);
+    KRR_RET(launch_mean(ctx, X, n, d, mu));
+    KRR_RET(launch_pack(ctx, X, n, d, mu, ctx->s, ctx->P));
+    return KRR_OK;
+}
+
+}  // namespace krr
+
+using namespace krr;
+
+extern "C" {
+
+int krr_default_opts(krr_opts* o) {
+    if (!o) return KRR_E_INVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->max_iter = 1000;
+    o->refine_max = 6;
+    o->oversample = 5;
+    o->check_every = 1;
+    o->inner_tol = 1e-4;
+    o->anchor_rtol = 1e-5;
+    o->precision = 0;
+    return KRR_OK;
+}
+
+int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
+    if (!out) return KRR_E_INVAL;
+    *out = nullptr;
+    krr_ctx* ctx = new krr_ctx();
+    if (opts) ctx->opts = *opts;
+    else krr_default_opts(&ctx->opts);
+    if (ctx->opts.max_iter < 1 || ctx->opts.refine_max < 1 || ctx->opts.oversample < 0 ||
+        ctx->opts.check_every < 1 || !(ctx->opts.inner_tol > 0.0) || ctx->opts.inner_tol >= 1.0 ||
+        !(ctx->opts.anchor_rtol >= 0.0)) {
+        delete ctx;
+        return KRR_E_INVAL;
+    }
+    ctx->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return KRR_E_CUDA;
+    }
+    if (cudaMalloc(&ctx->cg, sizeof(CGScalars)) != cudaSuccess ||
+        cudaMallocHost(&ctx->cg_host, sizeof(CGScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->cg) cudaFree(ctx->cg);
+        delete ctx;
+        return KRR_E_NOMEM;
+    }
+    *out = ctx;
+    return KRR_OK;
+}
+
+void krr_destroy(krr_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->prof_recs) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+    for (auto& kv : ctx->bufs)
+        if (kv.second.p) cudaFree(kv.second.p);
+    if (ctx->cg) cudaFree(ctx->cg);
+    if (ctx->cg_host) cudaFreeHost(ctx->cg_host);
+    delete ctx;
+}
+
+const char* krr_last_error(const krr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int krr_profile_enable(krr_ctx* ctx, int on) {
+    if (!ctx) return KRR_E_INVAL;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->prof_recs) {
+        ctx->prof_pool.push_back(r.start);
+        ctx->prof_pool.push_back(r.stop);
+    }
+    ctx->prof_recs.clear();
+    ctx->prof = on != 0;
+    return KRR_OK;
+}
+
+int krr_profile_read(krr_ctx* ctx, const char* phase, double* total_ms, long long* count) {
+    if (!ctx || !phase || !total_ms || !count) return KRR_E_INVAL;
+    int id = -1;
+    for (int i = 0; i < PH_COUNT; ++i)
+        if (std::strcmp(phase, kPhaseNames[i]) == 0) id = i;
+    if (id < 0) return fail(ctx, KRR_E_INVAL, std::string("unknown phase ") + phase);
+    double tot = 0.0;
+    long long cnt = 0;
+    for (auto& r : ctx->prof_recs) {
+        if (r.phase != id) continue;
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.stop) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, r.start, r.stop) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, KRR_E_CUDA, "profile event read failed");
+        }
+        tot += ms;
+        ++cnt;
+    }
+    *total_ms = tot;
+    *count = cnt;
+    return KRR_OK;
+}
+
+long long krr_launch_count(const krr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc, int d,
+             double sigma, double beta, const float* V, int nrhs, float* Q) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, Xr, nr, d));
+    KRR_RET(check_points(ctx, Xc, nc, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, beta, false));
+    if (!V || !Q) return fail(ctx, KRR_E_INVAL, "null V or Q");
+    if (nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "nrhs must be in [1, 16]");
+    if (beta != 0.0 && nr != nc) return fail(ctx, KRR_E_INVAL, "beta needs a square product");
+    const int ps = packed_stride(d);
+    const double s = LOG2E / (2.0 * sigma * sigma);
+    double* mu;
+    float *Pc, *Pr;
+    KRR_RET(bufT(ctx, "kmvm_mu", (size_t)d, &mu));
+    KRR_RET(bufT(ctx, "kmvm_Pc", (size_t)nc * ps, &Pc));
+    KRR_RET(launch_mean(ctx, Xc, nc, d, mu));
+    KRR_RET(launch_pack(ctx, Xc, nc, d, mu, s, Pc));
+    if (Xr == Xc && nr == nc) {
+        Pr = Pc;
+    } else {
+        KRR_RET(bufT(ctx, "kmvm_Pr", (size_t)nr * ps, &Pr));
+        KRR_RET(launch_pack(ctx, Xr, nr, d, mu, s, Pr));
+    }
+    KRR_RET(launch_kmvm(ctx, Pr, nr, Pc, nc, d, (float)beta, V, nrhs, Q));
+    return KRR_OK;
+}
+
+int krr_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                    const float* Y, const double* A, int nrhs, double* R) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, X, n, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, beta, false));
+    if (!Y || !A || !R) return fail(ctx, KRR_E_INVAL, "null Y, A or R");
+    if (nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "nrhs must be in [1, 16]");
+    return launch_residual_hp(ctx, X, n, d, sigma, beta, Y, A, nrhs, R);
+}
+
+int krr_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, float* OmT) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!OmT || l < 1 || n < 1) return fail(ctx, KRR_E_INVAL, "bad omega arguments");
+    return launch_omega(ctx, seed, l, n, l, OmT);
+}
+
+static int sketch_internal(krr_ctx* ctx, long long n, int l, unsigned long long seed, float** Yout,
+                           int* ldy) {
+    const int ld = (l + 3) / 4 * 4;
+    float *Om, *Y;
+    KRR_RET(bufT(ctx, "omega", (size_t)n * ld, &Om));
+    KRR_RET(bufT(ctx, "sketch", (size_t)n * ld, &Y));
+    {
+        Phase ph(ctx, PH_OMEGA);
+        KRR_RET(launch_omega(ctx, seed, l, n, ld, Om));
+    }
+    Phase ph(ctx, PH_SKETCH);
+    KRR_RET(launch_kgemm(ctx, ctx->P, n, ctx->P, n, ctx->d, Om, ld, ld, Y, ld));
+    *Yout = Y;
+    *ldy = ld;
+    return KRR_OK;
+}
+
+int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, int l,
+               unsigned long long seed, float* Y) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, X, n, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, 0.0, false));
+    if (!Y || l < 1) return fail(ctx, KRR_E_INVAL, "bad sketch arguments");
+    // uses the build state's packed points; the build state is reset
+    KRR_RET(build_common(ctx, X, n, d, sigma, 1.0));
+    float* Yi;
+    int ld;
+    KRR_RET(sketch_internal(ctx, n, l, seed, &Yi, &ld));
+    KRR_TRY_CUDA(cudaMemcpy2DAsync(Y, sizeof(float) * l, Yi, sizeof(float) * ld, sizeof(float) * l,
+                                   n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return KRR_OK;
+}
+
+int krr_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int k, int* piv, float* rdiag) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!Y || !piv || !rdiag || n < 1 || l < 1 || k < 1 || k > n)
+        return fail(ctx, KRR_E_INVAL, "bad qrcp arguments");
+    return launch_qrcp(ctx, Y, n, l, l, k, piv, rdiag);
+}
+
+int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                      int k, unsigned long long seed) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, X, n, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, beta, true));
+    if (k < 1 || k > n) return fail(ctx, KRR_E_INVAL, "k must be in [1, n]");
+    const double t0 = now_ms();
+    KRR_RET(build_common(ctx, X, n, d, sigma, beta));
+    const int l = (int)std::min<long long>(n, (long long)k + ctx->opts.oversample);
+    if (l > 4096) return fail(ctx, KRR_E_INVAL, "k + oversample must be <= 4096");
+    ctx->k = k;
+    ctx->l = l;
+    float* Y;
+    int ld;
+    KRR_RET(sketch_internal(ctx, n, l, seed, &Y, &ld));
+    int* piv;
+    float* rdiag;
+    KRR_RET(bufT(ctx, "piv", (size_t)k, &piv));
+    KRR_RET(bufT(ctx, "rdiag", (size_t)k, &rdiag));
+    {
+        Phase ph(ctx, PH_QRCP);
+        KRR_RET(launch_qrcp(ctx, Y, n, l, ld, k, piv, rdiag));
+    }
+    std::vector<float> rd(k);
+    KRR_TRY_CUDA(cudaMemcpyAsync(rd.data(), rdiag, sizeof(float) * k, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    int k_eff = 0;
+    const float thr = (float)(ctx->opts.anchor_rtol * rd[0]);
+    while (k_eff < k && rd[k_eff] > thr && std::isfinite(rd[k_eff])) ++k_eff;
+    if (k_eff < 1) return fail(ctx, KRR_E_NONFINITE, "sketch has no nonzero pivot");
+    KRR_RET(build_from_anchors(ctx, piv, k_eff));
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->build_ms = now_ms() - t0;
+    ctx->built = true;
+    return KRR_OK;
+}
+
+int krr_build_precond_anchors(krr_ctx* ctx, const float* X, long long n, int d, double sigma,
+                              double beta, const int* S, int k) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, X, n, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, beta, true));
+    if (!S || k < 1 || k > n) return fail(ctx, KRR_E_INVAL, "bad anchors");
+    std::vector<int> hs(k);
+    KRR_TRY_CUDA(cudaMemcpyAsync(hs.data(), S, sizeof(int) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int a = 0; a < k; ++a)
+        if (hs[a] < 0 || hs[a] >= n) return fail(ctx, KRR_E_INVAL, "anchor index out of range");
+    const double t0 = now_ms();
+    KRR_RET(build_common(ctx, X, n, d, sigma, beta));
+    ctx->k = k;
+    ctx->l = 0;
+    KRR_RET(build_from_anchors(ctx, S, k));
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->build_ms = now_ms() - t0;
+    ctx->built = true;
+    return KRR_OK;
+}
+
+int krr_get_anchors(krr_ctx* ctx, int* S, int* k_eff) {
+    if (!ctx || !k_eff) return KRR_E_INVAL;
+    if (!ctx->built) return fail(ctx, KRR_E_STATE, "no preconditioner built");
+    *k_eff = ctx->k_eff;
+    if (S)
+        KRR_TRY_CUDA(cudaMemcpyAsync(S, ctx->S, sizeof(int) * ctx->k_eff, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    return KRR_OK;
+}
+
+int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!ctx->built) return fail(ctx, KRR_E_STATE, "no preconditioner built");
+    if (!In || !Out || nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "bad apply arguments");
+    return launch_apply_precond(ctx, In, nrhs, Out, nullptr);
+}
+
+int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol, double* alpha,
+              krr_solve_info* info) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!ctx->built) return fail(ctx, KRR_E_STATE, "krr_solve before krr_build_precond");
+    if (X != ctx->X) return fail(ctx, KRR_E_INVAL, "X differs from the built point set");
+    if (!Y || !alpha) return fail(ctx, KRR_E_INVAL, "null Y or alpha");
+    if (nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "nrhs must be in [1, 16]");
+    if (!(tol > 0.0) || !(tol < 1.0)) return fail(ctx, KRR_E_INVAL, "tol must be in (0, 1)");
+    const double t0 = now_ms();
+    const long long n = ctx->n;
+    const long long tot = n * nrhs;
+    const int nb = cg_vec_blocks(ctx);
+    double *r64, *ynorm2, *rnorm2;
+    float *rhs, *x, *r, *z, *p, *q;
+    double *part1, *part2, *part3;
+    KRR_RET(bufT(ctx, "sv_r64", (size_t)tot, &r64));
+    KRR_RET(bufT(ctx, "sv_yn", (size_t)KRR_MAX_RHS, &ynorm2));
+    KRR_RET(bufT(ctx, "sv_rn", (size_t)KRR_MAX_RHS, &rnorm2));
+    KRR_RET(bufT(ctx, "sv_x", (size_t)tot, &x));
+    KRR_RET(bufT(ctx, "sv_r", (size_t)tot, &r));
+    KRR_RET(bufT(ctx, "sv_z", (size_t)tot, &z));
+    KRR_RET(bufT(ctx, "sv_p", (size_t)tot, &p));
+    KRR_RET(bufT(ctx, "sv_q", (size_t)tot, &q));
+    KRR_RET(bufT(ctx, "sv_part1", (size_t)nb * nrhs, &part1));
+    KRR_RET(bufT(ctx, "sv_part2", (size_t)nb * nrhs, &part2));
+    KRR_RET(bufT(ctx, "sv_part3", (size_t)nb * nrhs, &part3));
+    (void)rhs;
+
+    std::vector<double> yn(nrhs), rn(nrhs);
+    KRR_RET(launch_dot(ctx, Y, Y, n, nrhs, ynorm2));
+    KRR_TRY_CUDA(cudaMemcpyAsync(yn.data(), ynorm2, sizeof(double) * nrhs, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    KRR_TRY_CUDA(cudaMemsetAsync(alpha, 0, sizeof(double) * tot, ctx->stream));
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < nrhs; ++c)
+        if (!std::isfinite(yn[c])) return fail(ctx, KRR_E_NONFINITE, "non-finite right-hand side");
+
+    krr_solve_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.k_eff = ctx->k_eff;
+    inf.build_ms = ctx->build_ms;
+    const double tol2_inner = ctx->opts.inner_tol * ctx->opts.inner_tol;
+    int status = KRR_E_NOCONV;
+    for (int sweep = 0;; ++sweep) {
+        // residual of the current alpha (exactly y for alpha = 0)
+        if (sweep == 0) {
+            KRR_RET(launch_convert_up(ctx, Y, r64, tot));
+            for (int c = 0; c < nrhs; ++c) rn[c] = yn[c];
+        } else {
+            {
+                Phase ph(ctx, PH_RESID);
+                KRR_RET(launch_residual_hp(ctx, ctx->X, n, ctx->d, ctx->sigma, ctx->beta, Y, alpha,
+                                           nrhs, r64));
+            }
+            KRR_RET(launch_dot64(ctx, r64, r64, n, nrhs, rnorm2));
+            KRR_TRY_CUDA(cudaMemcpyAsync(rn.data(), rnorm2, sizeof(double) * nrhs,
+                                         cudaMemcpyDeviceToHost, ctx->stream));
+            KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        }
+        bool done = true;
+        for (int c = 0; c < nrhs; ++c) {
+            const double rel = yn[c] > 0.0 ? std::sqrt(rn[c] / yn[c]) : 0.0;
+            inf.rel_residual[c] = rel;
+            if (!std::isfinite(rel)) return fail(ctx, KRR_E_NONFINITE, "non-finite residual");
+            if (rel > tol) done = false;
+        }
+        inf.sweeps = sweep;
+        if (done) {
+            status = KRR_OK;
+            break;
+        }
+        if (sweep >= ctx->opts.refine_max) break;
+
+        // inner PCG on A delta = r (FP32), to relative accuracy inner_tol
+        KRR_RET(launch_convert(ctx, r64, r, tot));
+        KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+        {
+            Phase ph(ctx, PH_APPLY);
+            KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part1));
+        }
+        KRR_RET(launch_cg_start(ctx, r, z, nrhs, part1, part2));
+        KRR_TRY_CUDA(cudaMemcpyAsync(p, z, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
+        int it = 0;
+        while (it < ctx->opts.max_iter) {
+            {
+                Phase ph(ctx, PH_KMVM);
+                KRR_RET(launch_kmvm(ctx, ctx->P, n, ctx->P, n, ctx->d, (float)ctx->beta, p, nrhs, q));
+            }
+            inf.mvm_count++;
+            {
+                Phase ph(ctx, PH_CGVEC);
+                KRR_RET(launch_cg_alpha(ctx, p, q, nrhs, part1));
+                KRR_RET(launch_cg_update_xr(ctx, x, r, p, q, nrhs, part2, tol2_inner));
+            }
+            ++it;
+            if (it % ctx->opts.check_every == 0 || it == ctx->opts.max_iter) {
+                KRR_TRY_CUDA(cudaMemcpyAsync(ctx->cg_host, ctx->cg, sizeof(CGScalars),
+                                             cudaMemcpyDeviceToHost, ctx->stream));
+                KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+                if (ctx->cg_host->bad) break;
+                if (ctx->cg_host->all_done) break;
+            }
+            {
+                Phase ph(ctx, PH_APPLY);
+                KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part3));
+            }
+            {
+                Phase ph(ctx, PH_CGVEC);
+                KRR_RET(launch_cg_beta_p(ctx, p, z, nrhs, part3));
+            }
+        }
+        inf.iters += it;
+        KRR_RET(launch_accumulate(ctx, x, alpha, tot));
+    }
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    inf.status = status;
+    inf.solve_ms = now_ms() - t0;
+    if (info) *info = inf;
+    if (status != KRR_OK) fail(ctx, status, "tolerance not reached");
+    return status;
+}
+
+int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alpha, int nrhs,
+                float* f) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!ctx->built) return fail(ctx, KRR_E_STATE, "krr_predict before krr_build_precond");
+    KRR_RET(check_points(ctx, Xtest, m, ctx->d));
+    if (!alpha || !f) return fail(ctx, KRR_E_INVAL, "null alpha or f");
+    if (nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "nrhs must be in [1, 16]");
+    float* Pt;
+    double* mu;
+    KRR_RET(bufT(ctx, "pred_P", (size_t)m * ctx->ps, &Pt));
+    KRR_RET(bufT(ctx, "mu", (size_t)ctx->d, &mu));
+    KRR_RET(launch_pack(ctx, Xtest, m, ctx->d, mu, ctx->s, Pt));
+    return launch_kmvm(ctx, Pt, m, ctx->P, ctx->n, ctx->d, 0.f, alpha, nrhs, f);
+}
+
+}  // extern "C"

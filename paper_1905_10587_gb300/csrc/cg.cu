@@ -1,0 +1,416 @@
+// Conjugate-gradient vector kernels (Algorithm 5 step 3) and the Woodbury
+// application of the preconditioner (Algorithm 4, Eq. woodbury).
+//
+// Vectors are FP32, RHS-major (column q of an n x nrhs block at q*n); every dot
+// product is accumulated in FP64 and the CG scalars live in a small device struct,
+// so the recurrences run without host round trips.  The preconditioner is
+//     M^{-1} r = (r - F G^{-1} F^T r) / beta,   G = beta I + F^T F = L2 L2^T,
+// with F = K(X, X_S) L1^{-T} stored (n x ldF) and T2 = L2^{-1} held explicitly,
+// so one application is two streaming passes over F and two k x k triangular
+// products in FP64.
+#include "internal.cuh"
+
+#include <algorithm>
+
+namespace krr {
+
+constexpr int VT = 256;   // threads of the streaming kernels
+
+static int vec_blocks(krr_ctx* ctx, long long n) {
+    return (int)std::max<long long>(1, std::min<long long>(2LL * ctx->num_sms, ceil_div(n, VT)));
+}
+
+// Block-wide FP64 sum into part[q * gridDim.x + blockIdx.x].
+__device__ __forceinline__ void block_sum_store(double v, double* part, int q) {
+    __shared__ double red[VT / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < VT / 32; ++i) s += red[i];
+        part[(size_t)q * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(VT)
+k_dot_part(const float* __restrict__ A, const float* __restrict__ B, long long n, int nrhs,
+           double* __restrict__ part) {
+    for (int q = 0; q < nrhs; ++q) {
+        double s = 0.0;
+        for (long long i = (long long)blockIdx.x * VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+            s += (double)A[q * n + i] * (double)B[q * n + i];
+        block_sum_store(s, part, q);
+    }
+}
+
+__global__ void __launch_bounds__(VT)
+k_dot64_part(const double* __restrict__ A, const double* __restrict__ B, long long n, int nrhs,
+             double* __restrict__ part) {
+    for (int q = 0; q < nrhs; ++q) {
+        double s = 0.0;
+        for (long long i = (long long)blockIdx.x * VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+            s = fma(A[q * n + i], B[q * n + i], s);
+        block_sum_store(s, part, q);
+    }
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int nblk, int nrhs, double* out) {
+    const int q = threadIdx.x;
+    if (q >= nrhs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
+    out[q] = s;
+}
+
+int launch_dot(krr_ctx* ctx, const float* A, const float* B, long long n, int nrhs, double* out) {
+    const int nb = vec_blocks(ctx, n);
+    double* part;
+    KRR_RET(bufT(ctx, "dot_part", (size_t)nb * nrhs, &part));
+    k_dot_part<<<nb, VT, 0, ctx->stream>>>(A, B, n, nrhs, part);
+    KRR_CHECK_LAUNCH();
+    k_sum_parts<<<1, 32, 0, ctx->stream>>>(part, nb, nrhs, out);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+int launch_dot64(krr_ctx* ctx, const double* A, const double* B, long long n, int nrhs, double* out) {
+    const int nb = vec_blocks(ctx, n);
+    double* part;
+    KRR_RET(bufT(ctx, "dot_part", (size_t)nb * nrhs, &part));
+    k_dot64_part<<<nb, VT, 0, ctx->stream>>>(A, B, n, nrhs, part);
+    KRR_CHECK_LAUNCH();
+    k_sum_parts<<<1, 32, 0, ctx->stream>>>(part, nb, nrhs, out);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+// ------------------------------------------------------------------ Woodbury apply
+// u_part[blk][q][a] = sum_{i in chunk(blk)} F[i, a] R[q, i]   (a < k, 8 columns per thread)
+template <int NQ>
+__global__ void __launch_bounds__(VT)
+k_gemv_t(const float* __restrict__ F, long long n, int k, int ldF, const float* __restrict__ R,
+         long long ldr, long long rows_per, float* __restrict__ upart) {
+    constexpr int KA = 8;
+    const long long r0 = (long long)blockIdx.x * rows_per;
+    const long long r1 = min(n, r0 + rows_per);
+    for (int a0 = 0; a0 < k; a0 += KA * VT) {
+        float acc[KA][NQ];
+#pragma unroll
+        for (int m = 0; m < KA; ++m)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[m][q] = 0.f;
+        for (long long i = r0; i < r1; ++i) {
+            float rv[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) rv[q] = R[q * ldr + i];
+            const float* fr = F + i * ldF;
+#pragma unroll
+            for (int m = 0; m < KA; ++m) {
+                const int a = a0 + m * VT + threadIdx.x;
+                const float f = (a < k) ? fr[a] : 0.f;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[m][q] = fmaf(f, rv[q], acc[m][q]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < KA; ++m) {
+            const int a = a0 + m * VT + threadIdx.x;
+            if (a < k)
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    upart[((size_t)blockIdx.x * NQ + q) * k + a] = acc[m][q];
+        }
+    }
+}
+
+// u[q][a] = sum_blk upart (FP64)
+__global__ void k_gemv_t_reduce(const float* __restrict__ upart, int nblk, int nq, int k,
+                                double* __restrict__ u) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nq * k) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += (double)upart[(size_t)b * nq * k + e];
+    u[e] = s;
+}
+
+// y[q][a] = sum_b T[a][b] x[q][b] over b <= a (lower) or b >= a (upper).  One warp per row a.
+__global__ void k_tri_gemv(const double* __restrict__ T, int k, const double* __restrict__ x,
+                           int nq, bool lower, double* __restrict__ y) {
+    const int a = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (a >= k) return;
+    const int b0 = lower ? 0 : a, b1 = lower ? a + 1 : k;
+    for (int q = 0; q < nq; ++q) {
+        double s = 0.0;
+        for (int b = b0 + lane; b < b1; b += 32) s = fma(T[(size_t)a * k + b], x[(size_t)q * k + b], s);
+        s = warp_sum(s);
+        if (lane == 0) y[(size_t)q * k + a] = s;
+    }
+}
+
+// Z[q][i] = (R[q][i] - sum_a F[i, a] v[q][a]) / beta; one warp per row.  Optional partial R.Z.
+template <int NQ>
+__global__ void __launch_bounds__(VT)
+k_gemv_n_apply(const float* __restrict__ F, long long n, int k, int ldF, const double* __restrict__ v,
+               const float* __restrict__ R, long long ldr, float inv_beta, float* __restrict__ Z,
+               double* __restrict__ rz_part) {
+    extern __shared__ float sv[];   // NQ x k
+    for (int e = threadIdx.x; e < NQ * k; e += VT) sv[e] = (float)v[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double rz[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) rz[q] = 0.0;
+    for (long long i = (long long)blockIdx.x * (VT / 32) + w; i < n; i += (long long)gridDim.x * (VT / 32)) {
+        float s[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) s[q] = 0.f;
+        const float* fr = F + i * ldF;
+        for (int a = lane; a < k; a += 32) {
+            const float f = fr[a];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) s[q] = fmaf(f, sv[q * k + a], s[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float t = warp_sum(s[q]);
+            if (lane == 0) {
+                const float r = R[q * ldr + i];
+                const float z = (r - t) * inv_beta;
+                Z[q * ldr + i] = z;
+                rz[q] += (double)r * (double)z;
+            }
+        }
+    }
+    if (rz_part) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) block_sum_store(lane == 0 ? rz[q] : 0.0, rz_part, q);
+    }
+}
+
+typedef void (*gemv_t_fn)(const float*, long long, int, int, const float*, long long, long long, float*);
+typedef void (*gemv_n_fn)(const float*, long long, int, int, const double*, const float*, long long,
+                          float, float*, double*);
+
+// Z = M^{-1} R for nrhs columns.  When rz_part is non-null it receives per-block partial
+// sums of R.Z laid out [q][blk] with vec_blocks(n) blocks per column.
+int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part) {
+    const long long n = ctx->n;
+    const int k = ctx->k_eff;
+    const int nb = vec_blocks(ctx, n);
+    const long long rows_per = ceil_div(n, nb);
+    float* upart;
+    double *u, *u1, *v;
+    KRR_RET(bufT(ctx, "ap_upart", (size_t)nb * 4 * k, &upart));
+    KRR_RET(bufT(ctx, "ap_u", (size_t)4 * k, &u));
+    KRR_RET(bufT(ctx, "ap_u1", (size_t)4 * k, &u1));
+    KRR_RET(bufT(ctx, "ap_v", (size_t)4 * k, &v));
+    const float inv_beta = (float)(1.0 / ctx->beta);
+    for (int q0 = 0; q0 < nrhs; q0 += 4) {
+        const int nq = std::min(4, nrhs - q0);
+        gemv_t_fn gt = nq == 1 ? &k_gemv_t<1> : nq == 2 ? &k_gemv_t<2> : nq == 3 ? &k_gemv_t<3> : &k_gemv_t<4>;
+        gemv_n_fn gn = nq == 1 ? &k_gemv_n_apply<1> : nq == 2 ? &k_gemv_n_apply<2>
+                     : nq == 3 ? &k_gemv_n_apply<3> : &k_gemv_n_apply<4>;
+        const float* Rq = R + (size_t)q0 * n;
+        float* Zq = Z + (size_t)q0 * n;
+        gt<<<nb, VT, 0, ctx->stream>>>(ctx->F, n, k, ctx->ldF, Rq, n, rows_per, upart);
+        KRR_CHECK_LAUNCH();
+        k_gemv_t_reduce<<<ceil_div((long long)nq * k, 256), 256, 0, ctx->stream>>>(upart, nb, nq, k, u);
+        KRR_CHECK_LAUNCH();
+        k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2, k, u, nq, true, u1);
+        KRR_CHECK_LAUNCH();
+        k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2t, k, u1, nq, false, v);
+        KRR_CHECK_LAUNCH();
+        const size_t smem = sizeof(float) * nq * k;
+        if (smem > 48 * 1024) {
+            KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)gn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        }
+        gn<<<nb, VT, smem, ctx->stream>>>(ctx->F, n, k, ctx->ldF, v, Rq, n, inv_beta, Zq,
+                                          rz_part ? rz_part + (size_t)q0 * nb : nullptr);
+        KRR_CHECK_LAUNCH();
+    }
+    return KRR_OK;
+}
+
+// ------------------------------------------------------------------ PCG recurrences
+// a_q = rz_q / (p_q . q_q) for active columns; zero otherwise.
+__global__ void k_cg_alpha(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs) {
+    const int q = threadIdx.x;
+    if (q >= nrhs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
+    cg->pq[q] = s;
+    double a = 0.0;
+    if (cg->active[q]) {
+        if (!(s > 0.0) || !isfinite(s) || !isfinite(cg->rz[q])) {
+            cg->bad = 1;
+            cg->active[q] = 0;
+        } else {
+            a = cg->rz[q] / s;
+        }
+    }
+    cg->a[q] = a;
+}
+
+// x += a p; r -= a q; partial r.r
+__global__ void __launch_bounds__(VT)
+k_cg_update_xr(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
+               const float* __restrict__ qv, long long n, int nrhs, const CGScalars* __restrict__ cg,
+               double* __restrict__ part) {
+    for (int q = 0; q < nrhs; ++q) {
+        const float a = (float)cg->a[q];
+        double s = 0.0;
+        for (long long i = (long long)blockIdx.x * VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+            const long long e = q * n + i;
+            const float rv = fmaf(-a, qv[e], r[e]);
+            x[e] = fmaf(a, p[e], x[e]);
+            r[e] = rv;
+            s += (double)rv * (double)rv;
+        }
+        block_sum_store(s, part, q);
+    }
+}
+
+// rr_q = sum part; column q stays active while rr_q > tol2 * rr0_q.
+__global__ void k_cg_check(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs,
+                           double tol2) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    const int q = threadIdx.x;
+    if (q < nrhs) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
+        cg->rr[q] = s;
+        if (!isfinite(s)) {
+            cg->bad = 1;
+            cg->active[q] = 0;
+        }
+        if (cg->active[q] && !(s > tol2 * cg->rr0[q])) cg->active[q] = 0;
+        if (cg->active[q]) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cg->all_done = any ? 0 : 1;
+}
+
+// b_q = rz_new / rz; rz = rz_new
+__global__ void k_cg_beta(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs) {
+    const int q = threadIdx.x;
+    if (q >= nrhs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
+    const double rz = cg->rz[q];
+    cg->b[q] = (rz != 0.0 && isfinite(s)) ? s / rz : 0.0;
+    cg->rz[q] = s;
+}
+
+// p = z + b p
+__global__ void __launch_bounds__(VT)
+k_cg_update_p(float* __restrict__ p, const float* __restrict__ z, long long n, int nrhs,
+              const CGScalars* __restrict__ cg) {
+    const long long tot = n * nrhs;
+    for (long long e = (long long)blockIdx.x * VT + threadIdx.x; e < tot; e += (long long)gridDim.x * VT) {
+        const int q = (int)(e / n);
+        p[e] = fmaf((float)cg->b[q], p[e], z[e]);
+    }
+}
+
+// start: rz = part sum (r.z), rr0 = r.r given in rr0_part, active = rr0 > 0
+__global__ void k_cg_init(CGScalars* cg, const double* __restrict__ rz_part,
+                          const double* __restrict__ rr_part, int nblk, int nrhs) {
+    const int q = threadIdx.x;
+    if (threadIdx.x == 0) {
+        cg->all_done = 0;
+        cg->bad = 0;
+    }
+    if (q >= nrhs) return;
+    double s = 0.0, t = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        s += rz_part[(size_t)q * nblk + b];
+        t += rr_part[(size_t)q * nblk + b];
+    }
+    cg->rz[q] = s;
+    cg->rr0[q] = t;
+    cg->rr[q] = t;
+    cg->active[q] = (t > 0.0 && isfinite(t) && isfinite(s)) ? 1 : 0;
+    cg->a[q] = 0.0;
+    cg->b[q] = 0.0;
+}
+
+// out32 = (float) in64 ; and alpha64 += x32
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, long long tot) {
+    for (long long e = (long long)blockIdx.x * VT + threadIdx.x; e < tot; e += (long long)gridDim.x * VT)
+        b[e] = (float)a[e];
+}
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, long long tot) {
+    for (long long e = (long long)blockIdx.x * VT + threadIdx.x; e < tot; e += (long long)gridDim.x * VT)
+        b[e] = (double)a[e];
+}
+__global__ void k_axpy_f32_into_f64(const float* __restrict__ x, double* __restrict__ y, long long tot) {
+    for (long long e = (long long)blockIdx.x * VT + threadIdx.x; e < tot; e += (long long)gridDim.x * VT)
+        y[e] += (double)x[e];
+}
+
+// ---- host drivers for the recurrences (launch sequences; no host sync inside)
+int cg_vec_blocks(krr_ctx* ctx) { return vec_blocks(ctx, ctx->n); }
+
+int launch_cg_start(krr_ctx* ctx, const float* r, const float* z, int nrhs, double* rz_part,
+                    double* rr_part) {
+    const int nb = vec_blocks(ctx, ctx->n);
+    k_dot_part<<<nb, VT, 0, ctx->stream>>>(r, r, ctx->n, nrhs, rr_part);
+    KRR_CHECK_LAUNCH();
+    k_cg_init<<<1, 32, 0, ctx->stream>>>(ctx->cg, rz_part, rr_part, nb, nrhs);
+    KRR_CHECK_LAUNCH();
+    (void)z;
+    return KRR_OK;
+}
+
+int launch_cg_alpha(krr_ctx* ctx, const float* p, const float* q, int nrhs, double* part) {
+    const int nb = vec_blocks(ctx, ctx->n);
+    k_dot_part<<<nb, VT, 0, ctx->stream>>>(p, q, ctx->n, nrhs, part);
+    KRR_CHECK_LAUNCH();
+    k_cg_alpha<<<1, 32, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+int launch_cg_update_xr(krr_ctx* ctx, float* x, float* r, const float* p, const float* q, int nrhs,
+                        double* part, double tol2) {
+    const int nb = vec_blocks(ctx, ctx->n);
+    k_cg_update_xr<<<nb, VT, 0, ctx->stream>>>(x, r, p, q, ctx->n, nrhs, ctx->cg, part);
+    KRR_CHECK_LAUNCH();
+    k_cg_check<<<1, 32, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs, tol2);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const double* rz_part) {
+    const int nb = vec_blocks(ctx, ctx->n);
+    k_cg_beta<<<1, 32, 0, ctx->stream>>>(ctx->cg, rz_part, nb, nrhs);
+    KRR_CHECK_LAUNCH();
+    k_cg_update_p<<<nb, VT, 0, ctx->stream>>>(p, z, ctx->n, nrhs, ctx->cg);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot) {
+    k_f64_to_f32<<<vec_blocks(ctx, tot), VT, 0, ctx->stream>>>(a, b, tot);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_convert_up(krr_ctx* ctx, const float* a, double* b, long long tot) {
+    k_f32_to_f64<<<vec_blocks(ctx, tot), VT, 0, ctx->stream>>>(a, b, tot);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_accumulate(krr_ctx* ctx, const float* x, double* y, long long tot) {
+    k_axpy_f32_into_f64<<<vec_blocks(ctx, tot), VT, 0, ctx->stream>>>(x, y, tot);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+}  // namespace krr

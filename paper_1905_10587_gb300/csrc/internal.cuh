@@ -1,0 +1,203 @@
+// Internal declarations shared by the CUDA translation units of libkrr.
+// Not part of the public ABI (see include/krr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/krr.h"
+
+namespace krr {
+
+// ---------------------------------------------------------------- status
+struct Status {
+    int code = KRR_OK;
+    std::string msg;
+};
+
+#define KRR_TRY_CUDA(call)                                                            \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return ::krr::fail(ctx, KRR_E_CUDA, std::string(#call) + ": " +           \
+                               cudaGetErrorString(e_));                               \
+    } while (0)
+
+#define KRR_CHECK_LAUNCH()                                                            \
+    do {                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess)                                                        \
+            return ::krr::fail(ctx, KRR_E_CUDA, std::string("launch: ") +             \
+                               cudaGetErrorString(e_));                               \
+        ctx->launches++;                                                              \
+    } while (0)
+
+#define KRR_RET(expr)                    \
+    do {                                 \
+        int rc_ = (expr);                \
+        if (rc_ != KRR_OK) return rc_;   \
+    } while (0)
+
+// Packed point: PS floats per point, PS = round_up(d + 1, 4):
+//   [ xh_0 .. xh_{d-1}, a, 0 ... ]   with xh = (x - mu) * sqrt(s), a = -||xh||^2,
+//   s = log2(e) / (2 sigma^2), so that K_ij = exp2(a_i + a_j + 2 xh_i . xh_j).
+// Kernel dimension used for a data dimension d: exact for d <= 16, else padded with
+// zero coordinates to one of the compiled sizes.
+inline int kernel_dim(int d) {
+    return d <= 16 ? d : d <= 24 ? 24 : d <= 32 ? 32 : d <= 48 ? 48 : 64;
+}
+inline int packed_stride(int d) { return (kernel_dim(d) + 1 + 3) / 4 * 4; }
+
+// Per-context device scalars of the PCG recurrences (one slot per RHS).
+struct CGScalars {
+    double rz[KRR_MAX_RHS];
+    double rz_new[KRR_MAX_RHS];
+    double pq[KRR_MAX_RHS];
+    double rr[KRR_MAX_RHS];
+    double rr0[KRR_MAX_RHS];
+    double a[KRR_MAX_RHS];
+    double b[KRR_MAX_RHS];
+    int active[KRR_MAX_RHS];
+    int all_done;
+    int bad;            // a non-finite or non-positive curvature was met
+};
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Phase timers: CUDA events bracketing a phase on the context's stream.
+struct PhaseRec {
+    cudaEvent_t start, stop;
+    int phase;
+};
+
+enum PhaseId { PH_KMVM = 0, PH_SKETCH, PH_OMEGA, PH_QRCP, PH_FGEMM, PH_GRAM, PH_CHOL, PH_APPLY,
+               PH_RESID, PH_CGVEC, PH_PREP, PH_COUNT };
+extern const char* const kPhaseNames[PH_COUNT];
+
+}  // namespace krr
+
+struct krr_ctx {
+    cudaStream_t stream = nullptr;
+    krr_opts opts{};
+    std::string err;
+    int device = 0;
+    int num_sms = 0;
+    long long launches = 0;
+    std::unordered_map<std::string, krr::Buf> bufs;
+
+    // ---- state of the last build
+    bool built = false;
+    const float* X = nullptr;   // caller's point set (not owned)
+    long long n = 0;
+    int d = 0, ps = 0;
+    double sigma = 0, beta = 0, s = 0;   // s = log2(e)/(2 sigma^2)
+    int k = 0, k_eff = 0, l = 0, ldF = 0;
+    double build_ms = 0;
+    // device arrays (views into bufs)
+    float* P = nullptr;        // n x ps packed points of X
+    float* PS = nullptr;       // k_eff x ps packed anchors
+    float* XS = nullptr;       // k_eff x d raw anchor coordinates
+    int* S = nullptr;          // k_eff anchor indices
+    float* F = nullptr;        // n x ldF, F = K(X, X_S) L1^{-T}
+    double* T2 = nullptr;      // k_eff x k_eff, L2^{-1} (lower)
+    double* T2t = nullptr;     // its transpose
+    krr::CGScalars* cg = nullptr;
+    krr::CGScalars* cg_host = nullptr;   // pinned mirror
+
+    // ---- phase timers (off unless krr_profile_enable)
+    bool prof = false;
+    std::vector<krr::PhaseRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+namespace krr {
+
+int fail(krr_ctx* ctx, int code, const std::string& msg);
+
+// Brackets a phase with CUDA events when profiling is on (no-op otherwise).
+class Phase {
+  public:
+    Phase(krr_ctx* ctx, int id);
+    ~Phase();
+  private:
+    krr_ctx* ctx_;
+    int id_;
+    cudaEvent_t start_ = nullptr;
+};
+// Device buffer named `name`, at least `bytes` long (grown by reallocation).
+int buf(krr_ctx* ctx, const char* name, size_t bytes, void** out);
+template <class T>
+inline int bufT(krr_ctx* ctx, const char* name, size_t count, T** out) {
+    return buf(ctx, name, count * sizeof(T), reinterpret_cast<void**>(out));
+}
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ float ex2f(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------- launchers
+// kmvm.cu
+int launch_mean(krr_ctx* ctx, const float* X, long long n, int d, double* mu_dev);
+int launch_pack(krr_ctx* ctx, const float* X, long long n, int d, const double* mu_dev, double s,
+                float* P);
+int launch_gather_pack(krr_ctx* ctx, const float* P, int ps, const float* X, int d, const int* idx,
+                       int m, float* Pout, float* Xout);
+// Q = K(Pr, Pc) V + beta V (RHS-major, V: nc x nrhs, Q: nr x nrhs)
+int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
+                float beta, const float* V, int nrhs, float* Q);
+// R = Y - (K + beta I) A in FP64 (Y float, A/R double)
+int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                       const float* Y, const double* A, int nrhs, double* R);
+
+// sketch.cu
+int launch_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, int ld, float* OmT);
+// Out[i*ldo + a] = sum_j K(Pr_i, Pc_j) V[j*ldv + a], a < ncol (FP32 SIMT contraction)
+int launch_kgemm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
+                 const float* V, int ldv, int ncol, float* Out, int ldo);
+// G = beta I + F^T F (FP64 k x k, full), F: n x ldF
+int launch_gram(krr_ctx* ctx, const float* F, long long n, int k, int ldF, double beta, double* G);
+
+// qrcp.cu
+int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int* piv, float* rdiag);
+
+// dense64.cu
+int launch_kss(krr_ctx* ctx, const float* XS, int k, int d, double sigma, double* A);
+// In-place lower Cholesky of the k x k row-major A (upper part ignored).  Sets *info
+// (host) to 0 or to 1 + the failing column.
+int launch_potrf(krr_ctx* ctx, double* A, int k, int* info);
+// Solve L X = B in place (B k x k row-major), L lower k x k row-major.
+int launch_trsm_lower(krr_ctx* ctx, const double* L, double* B, int k);
+int launch_transpose64(krr_ctx* ctx, const double* A, double* At, int k);
+int launch_to_float_transposed(krr_ctx* ctx, const double* A, int k, float* Out, int ldo);
+int launch_set_identity(krr_ctx* ctx, double* A, int k);
+int launch_add_diag(krr_ctx* ctx, double* A, int k, double v);
+
+// cg.cu
+int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part_out);
+int launch_dot(krr_ctx* ctx, const float* A, const float* B, long long n, int nrhs, double* out);
+int launch_dot64(krr_ctx* ctx, const double* A, const double* B, long long n, int nrhs, double* out);
+
+}  // namespace krr

@@ -1,0 +1,443 @@
+// Tiled on-the-fly Gaussian kernel products (the discrete Gauss transform of
+// Section 2.3, Eq. dscrt_gt, evaluated exactly): K is never stored.
+//
+//   Q_i = sum_j exp2(a_i + a_j + 2 xh_i . xh_j) V_j  (+ beta V_i)
+//
+// with xh = (x - mu) sqrt(s), a = -||xh||^2 and s = log2(e) / (2 sigma^2), which
+// is exp(-||x_i - x_j||^2 / (2 sigma^2)).  Each CTA holds a block of rows in
+// registers and streams the column points through shared memory; the exponent is
+// d+1 FP32 FMAs, the exponential is one MUFU ex2, and each right-hand side costs
+// one more FMA.  Columns are split across CTAs (split-K) when the rows alone
+// cannot fill the 152 SMs; the partial sums then go through a small scratch
+// buffer and a deterministic reduction.
+//
+// Also here: the FP64 residual used by iterative refinement, which evaluates
+// the kernel from exact differences of the float32 coordinates in double.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+
+namespace krr {
+
+// ------------------------------------------------------------------ mean / pack
+__global__ void k_mean_partial(const float* __restrict__ X, long long n, int d,
+                               double* __restrict__ part) {
+    __shared__ double red[256];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int c = 0; c < d; ++c) {
+        double s = 0.0;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            s += (double)X[i * d + c];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * d + c] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_mean_final(const double* __restrict__ part, int nblk, int d, long long n,
+                             double* __restrict__ mu) {
+    int c = threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * d + c];
+    mu[c] = s / (double)n;
+}
+
+int launch_mean(krr_ctx* ctx, const float* X, long long n, int d, double* mu) {
+    const int nblk = (int)std::min<long long>(2 * ctx->num_sms, ceil_div(n, 256));
+    double* part;
+    KRR_RET(bufT(ctx, "mean_part", (size_t)nblk * d, &part));
+    k_mean_partial<<<nblk, 256, 0, ctx->stream>>>(X, n, d, part);
+    KRR_CHECK_LAUNCH();
+    k_mean_final<<<1, 64, 0, ctx->stream>>>(part, nblk, d, n, mu);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+__global__ void k_pack(const float* __restrict__ X, long long n, int d, int dk, int ps,
+                       const double* __restrict__ mu, double sq, float* __restrict__ P) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double nrm = 0.0;
+    float* out = P + i * ps;
+    for (int c = 0; c < ps; ++c) {
+        float v = 0.f;
+        if (c < d) v = (float)(((double)X[i * d + c] - mu[c]) * sq);
+        if (c < dk) {
+            out[c] = v;
+            nrm += (double)v * (double)v;
+        } else {
+            out[c] = 0.f;
+        }
+    }
+    out[dk] = (float)(-nrm);
+}
+
+int launch_pack(krr_ctx* ctx, const float* X, long long n, int d, const double* mu, double s,
+                float* P) {
+    const int dk = kernel_dim(d);
+    const int ps = packed_stride(d);
+    k_pack<<<ceil_div(n, 256), 256, 0, ctx->stream>>>(X, n, d, dk, ps, mu, std::sqrt(s), P);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+__global__ void k_gather_pack(const float* __restrict__ P, int ps, const float* __restrict__ X,
+                              int d, const int* __restrict__ idx, int m, float* __restrict__ Pout,
+                              float* __restrict__ Xout) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    long long i = idx[a];
+    for (int c = 0; c < ps; ++c) Pout[(size_t)a * ps + c] = P[i * ps + c];
+    if (Xout)
+        for (int c = 0; c < d; ++c) Xout[(size_t)a * d + c] = X[i * d + c];
+}
+
+int launch_gather_pack(krr_ctx* ctx, const float* P, int ps, const float* X, int d,
+                       const int* idx, int m, float* Pout, float* Xout) {
+    k_gather_pack<<<ceil_div(m, 128), 128, 0, ctx->stream>>>(P, ps, X, d, idx, m, Pout, Xout);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+// ------------------------------------------------------------------ FP32 tile MVM
+constexpr int KM_THREADS = 128;
+constexpr int KM_BN = 128;
+
+template <int D, int NRHS, int R>
+__global__ void __launch_bounds__(KM_THREADS, 4)
+k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
+       const float* __restrict__ V, int ldv, int tiles_per_split, float beta,
+       float* __restrict__ Q, int ldq, float* __restrict__ part) {
+    constexpr int PS = (D + 1 + 3) / 4 * 4;
+    constexpr int PS4 = PS / 4;
+    __shared__ float4 sP[KM_BN * PS4];
+    __shared__ __align__(16) float sV[KM_BN * NRHS];
+
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * (KM_THREADS * R);
+
+    float xi[R][D];
+    float ai[R];
+    float acc[R][NRHS];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = row0 + r * KM_THREADS + tid;
+        const bool ok = i < nr;
+#pragma unroll
+        for (int c = 0; c < D; ++c) xi[r][c] = ok ? 2.f * Pr[i * PS + c] : 0.f;
+        ai[r] = ok ? Pr[i * PS + D] : 0.f;
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) acc[r][q] = 0.f;
+    }
+
+    const int ntiles = (nc + KM_BN - 1) / KM_BN;
+    const int t0 = blockIdx.y * tiles_per_split;
+    const int t1 = min(t0 + tiles_per_split, ntiles);
+    const float4* Pc4 = reinterpret_cast<const float4*>(Pc);
+
+    for (int t = t0; t < t1; ++t) {
+        const int c0 = t * KM_BN;
+        for (int e = tid; e < KM_BN * PS4; e += KM_THREADS) {
+            const int j = e / PS4;
+            sP[e] = (c0 + j < nc) ? Pc4[(size_t)(c0 + j) * PS4 + (e - j * PS4)]
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = tid; e < KM_BN * NRHS; e += KM_THREADS) {
+            const int q = e / KM_BN, j = e - q * KM_BN;
+            sV[j * NRHS + q] = (c0 + j < nc) ? V[(size_t)q * ldv + c0 + j] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < KM_BN; ++j) {
+            float xj[PS];
+#pragma unroll
+            for (int w = 0; w < PS4; ++w) {
+                const float4 v = sP[j * PS4 + w];
+                xj[4 * w + 0] = v.x;
+                xj[4 * w + 1] = v.y;
+                xj[4 * w + 2] = v.z;
+                xj[4 * w + 3] = v.w;
+            }
+            float vj[NRHS];
+            if constexpr (NRHS % 4 == 0) {
+#pragma unroll
+                for (int w = 0; w < NRHS / 4; ++w) {
+                    const float4 v = reinterpret_cast<const float4*>(sV + j * NRHS)[w];
+                    vj[4 * w + 0] = v.x;
+                    vj[4 * w + 1] = v.y;
+                    vj[4 * w + 2] = v.z;
+                    vj[4 * w + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) vj[q] = sV[j * NRHS + q];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float tt = ai[r] + xj[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) tt = fmaf(xi[r][c], xj[c], tt);
+                const float e = ex2f(tt);
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) acc[r][q] = fmaf(e, vj[q], acc[r][q]);
+            }
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = row0 + r * KM_THREADS + tid;
+        if (i >= nr) continue;
+        if (part == nullptr) {
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+                Q[(size_t)q * ldq + i] =
+                    acc[r][q] + (beta != 0.f ? beta * V[(size_t)q * ldv + i] : 0.f);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+                part[((size_t)blockIdx.y * NRHS + q) * nr + i] = acc[r][q];
+        }
+    }
+}
+
+__global__ void k_kmvm_reduce(const float* __restrict__ part, int splits, int nr, int nrhs,
+                              const float* __restrict__ V, int ldv, float beta,
+                              float* __restrict__ Q, int ldq) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nr * nrhs) return;
+    const int q = (int)(e / nr);
+    const int i = (int)(e - (long long)q * nr);
+    float s = 0.f;
+    for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * nrhs + q) * nr + i];
+    if (beta != 0.f) s += beta * V[(size_t)q * ldv + i];
+    Q[(size_t)q * ldq + i] = s;
+}
+
+template <int D, int NRHS>
+constexpr int kmvm_rows() {
+    return (D > 32) ? 1 : (D > 16 || (NRHS >= 8 && D >= 8)) ? 2 : 4;
+}
+
+typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float,
+                        float*, int, float*);
+
+template <int D, int NRHS>
+static kmvm_fn pick2() {
+    return &k_kmvm<D, NRHS, kmvm_rows<D, NRHS>()>;
+}
+
+template <int D>
+static kmvm_fn pick1(int nrhs, int* R) {
+    switch (nrhs) {
+        case 1: *R = kmvm_rows<D, 1>(); return pick2<D, 1>();
+        case 2: *R = kmvm_rows<D, 2>(); return pick2<D, 2>();
+        case 4: *R = kmvm_rows<D, 4>(); return pick2<D, 4>();
+        case 8: *R = kmvm_rows<D, 8>(); return pick2<D, 8>();
+        case 16: *R = kmvm_rows<D, 16>(); return pick2<D, 16>();
+    }
+    return nullptr;
+}
+
+static kmvm_fn pick(int dk, int nrhs, int* R) {
+    switch (dk) {
+#define KRR_D(v) \
+    case v: return pick1<v>(nrhs, R);
+        KRR_D(1) KRR_D(2) KRR_D(3) KRR_D(4) KRR_D(5) KRR_D(6) KRR_D(7) KRR_D(8)
+        KRR_D(9) KRR_D(10) KRR_D(11) KRR_D(12) KRR_D(13) KRR_D(14) KRR_D(15) KRR_D(16)
+        KRR_D(24) KRR_D(32) KRR_D(48) KRR_D(64)
+#undef KRR_D
+    }
+    return nullptr;
+}
+
+static int occupancy(krr_ctx* ctx, const void* fn, int threads) {
+    static std::map<const void*, int> cache;
+    auto it = cache.find(fn);
+    if (it != cache.end()) return it->second;
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    cache[fn] = occ;
+    return occ;
+}
+
+// Number of column splits: fill the SMs with whole waves.
+static int choose_splits(int nblk, int ntiles, int slots) {
+    int best = 1;
+    double best_score = -1.0;
+    const int smax = std::max(1, std::min(ntiles, 64));
+    for (int s = 1; s <= smax; ++s) {
+        const double tot = (double)nblk * s;
+        const double waves = tot / slots;
+        const double score = waves >= 1.0 ? waves / std::ceil(waves) : waves;
+        if (score > best_score + 1e-9) {
+            best_score = score;
+            best = s;
+        }
+        if (waves >= 4.0) break;
+    }
+    return best;
+}
+
+int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
+                float beta, const float* V, int nrhs, float* Q) {
+    if (nr > 0x7fffffffLL || nc > 0x7fffffffLL)
+        return fail(ctx, KRR_E_INVAL, "kmvm: more than 2^31 points");
+    const int dk = kernel_dim(d);
+    int done = 0;
+    while (done < nrhs) {
+        const int left = nrhs - done;
+        const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        int R = 4;
+        kmvm_fn fn = pick(dk, chunk, &R);
+        if (!fn) return fail(ctx, KRR_E_INVAL, "kmvm: unsupported dimension");
+        const int rows_per = KM_THREADS * R;
+        const int nblk = (int)ceil_div(nr, rows_per);
+        const int ntiles = (int)ceil_div(nc, KM_BN);
+        const int slots = ctx->num_sms * occupancy(ctx, (const void*)fn, KM_THREADS);
+        int splits = choose_splits(nblk, ntiles, slots);
+        const int tps = (ntiles + splits - 1) / splits;
+        splits = (ntiles + tps - 1) / tps;
+        float* part = nullptr;
+        if (splits > 1)
+            KRR_RET(bufT(ctx, "kmvm_part", (size_t)splits * chunk * nr, &part));
+        dim3 grid(nblk, splits);
+        const float* Vc = V + (size_t)done * nc;
+        float* Qc = Q + (size_t)done * nr;
+        fn<<<grid, KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps, beta,
+                                                 Qc, (int)nr, part);
+        KRR_CHECK_LAUNCH();
+        if (splits > 1) {
+            const long long tot = nr * chunk;
+            k_kmvm_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, splits, (int)nr, chunk,
+                                                                        Vc, (int)nc, beta, Qc,
+                                                                        (int)nr);
+            KRR_CHECK_LAUNCH();
+        }
+        done += chunk;
+    }
+    return KRR_OK;
+}
+
+// ------------------------------------------------------------------ FP64 residual
+constexpr int HP_THREADS = 128;
+constexpr int HP_BN = 64;
+
+template <int DM, int NR>
+__global__ void __launch_bounds__(HP_THREADS)
+k_resid_hp(const float* __restrict__ X, int n, int d, double inv2s2, const double* __restrict__ A,
+           int tiles_per_split, double* __restrict__ part) {
+    __shared__ double sX[HP_BN * DM];
+    __shared__ double sA[HP_BN * NR];
+    const int tid = threadIdx.x;
+    const long long i = (long long)blockIdx.x * HP_THREADS + tid;
+    double xi[DM];
+#pragma unroll
+    for (int c = 0; c < DM; ++c) xi[c] = (i < n && c < d) ? (double)X[i * d + c] : 0.0;
+    double acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = 0.0;
+
+    const int ntiles = (n + HP_BN - 1) / HP_BN;
+    const int t0 = blockIdx.y * tiles_per_split;
+    const int t1 = min(t0 + tiles_per_split, ntiles);
+    for (int t = t0; t < t1; ++t) {
+        const int c0 = t * HP_BN;
+        for (int e = tid; e < HP_BN * DM; e += HP_THREADS) {
+            const int j = e / DM, c = e - j * DM;
+            sX[e] = (c0 + j < n && c < d) ? (double)X[(size_t)(c0 + j) * d + c] : 0.0;
+        }
+        for (int e = tid; e < HP_BN * NR; e += HP_THREADS) {
+            const int q = e / HP_BN, j = e - q * HP_BN;
+            sA[j * NR + q] = (c0 + j < n) ? A[(size_t)q * n + c0 + j] : 0.0;
+        }
+        __syncthreads();
+        for (int j = 0; j < HP_BN; ++j) {
+            double d2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < DM; ++c) {
+                const double df = xi[c] - sX[j * DM + c];
+                d2 = fma(df, df, d2);
+            }
+            const double kv = exp(-d2 * inv2s2);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q] = fma(kv, sA[j * NR + q], acc[q]);
+        }
+        __syncthreads();
+    }
+    if (i < n) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) part[((size_t)blockIdx.y * NR + q) * n + i] = acc[q];
+    }
+}
+
+__global__ void k_resid_reduce(const double* __restrict__ part, int splits, int n, int nr,
+                               const float* __restrict__ Y, const double* __restrict__ A,
+                               double beta, double* __restrict__ R) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nr) return;
+    const int q = (int)(e / n);
+    const int i = (int)(e - (long long)q * n);
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * nr + q) * n + i];
+    R[(size_t)q * n + i] = (double)Y[(size_t)q * n + i] - beta * A[(size_t)q * n + i] - s;
+}
+
+typedef void (*hp_fn)(const float*, int, int, double, const double*, int, double*);
+
+template <int DM>
+static hp_fn hp_pick1(int nr) {
+    switch (nr) {
+        case 1: return &k_resid_hp<DM, 1>;
+        case 2: return &k_resid_hp<DM, 2>;
+        case 4: return &k_resid_hp<DM, 4>;
+        case 8: return &k_resid_hp<DM, 8>;
+        case 16: return &k_resid_hp<DM, 16>;
+    }
+    return nullptr;
+}
+
+int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                       const float* Y, const double* A, int nrhs, double* R) {
+    if (n > 0x7fffffffLL) return fail(ctx, KRR_E_INVAL, "residual: more than 2^31 points");
+    const double inv2s2 = 1.0 / (2.0 * sigma * sigma);
+    int done = 0;
+    while (done < nrhs) {
+        const int left = nrhs - done;
+        const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        hp_fn fn = d <= 4 ? hp_pick1<4>(chunk) : d <= 8 ? hp_pick1<8>(chunk)
+                 : d <= 16 ? hp_pick1<16>(chunk) : hp_pick1<64>(chunk);
+        const int nblk = (int)ceil_div(n, HP_THREADS);
+        const int ntiles = (int)ceil_div(n, HP_BN);
+        const int slots = ctx->num_sms * occupancy(ctx, (const void*)fn, HP_THREADS);
+        int splits = choose_splits(nblk, ntiles, slots);
+        const int tps = (ntiles + splits - 1) / splits;
+        splits = (ntiles + tps - 1) / tps;
+        double* part;
+        KRR_RET(bufT(ctx, "hp_part", (size_t)splits * chunk * n, &part));
+        dim3 grid(nblk, splits);
+        fn<<<grid, HP_THREADS, 0, ctx->stream>>>(X, (int)n, d, inv2s2, A + (size_t)done * n, tps,
+                                                 part);
+        KRR_CHECK_LAUNCH();
+        const long long tot = n * chunk;
+        k_resid_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(
+            part, splits, (int)n, chunk, Y + (size_t)done * n, A + (size_t)done * n, beta,
+            R + (size_t)done * n);
+        KRR_CHECK_LAUNCH();
+        done += chunk;
+    }
+    return KRR_OK;
+}
+
+}  // namespace krr

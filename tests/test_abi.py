@@ -1,0 +1,59 @@
+"""Host-side checks of the C ABI library: it builds, loads and exports every entry
+point include/krr.h declares, and the binding's struct layouts match the header.
+No compute calls (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "krr.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(krr_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_10587_gb300 import build
+    from paper_1905_10587_gb300 import _lib
+    build()
+    return _lib.load()
+
+
+def test_header_declares_the_path():
+    names = _declared()
+    for must in ("krr_build_precond", "krr_solve", "krr_predict", "krr_kmvm", "krr_sketch",
+                 "krr_qrcp", "krr_precond_apply", "krr_residual_hp", "krr_omega"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_header_symbol():
+    from paper_1905_10587_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == _declared()
+
+
+def test_struct_layouts_match_header():
+    from paper_1905_10587_gb300 import _lib
+    assert C.sizeof(_lib.KrrOpts) == 4 * 4 + 8 * 2 + 4 * 8
+    assert _lib.KrrOpts.inner_tol.offset == 16
+    assert C.sizeof(_lib.KrrSolveInfo) == 16 + 8 * 16 + 16 + 4 * 8
+    assert _lib.KrrSolveInfo.build_ms.offset == 16 + 8 * 16
+
+
+def test_default_opts_without_gpu(lib):
+    from paper_1905_10587_gb300 import _lib
+    o = _lib.KrrOpts()
+    assert lib.krr_default_opts(C.byref(o)) == 0
+    assert o.oversample == 5 and o.max_iter > 0 and 0 < o.inner_tol < 1
+    assert lib.krr_default_opts(None) == 1
+    assert lib.krr_last_error(None) == b"null context"

@@ -1,0 +1,222 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs (needs a GB300).
+
+Tolerances: kernel products <= 1e-5 relative (norm-wise per column), the final
+solve residual <= 1e-6 relative measured by the oracle's FP64 product, and alpha
+within 1e-4 relative of the dense FP64 solve wherever the dense solve fits.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import krr_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_1905_10587_gb300.api import KRR
+    return KRR
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def _relcols(got, ref):
+    got = np.atleast_2d(np.asarray(got, dtype=np.float64).T).T
+    ref = np.atleast_2d(np.asarray(ref, dtype=np.float64).T).T
+    return np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+# ------------------------------------------------------------------ kernel products
+@pytest.mark.parametrize("n,d,nrhs,beta", [(2000, 4, 1, 1e-2), (1, 3, 1, 0.5), (127, 2, 3, 0.0),
+                                            (1000, 8, 16, 1e-3), (777, 13, 5, 0.1),
+                                            (300, 20, 2, 0.0), (130, 64, 1, 1.0)])
+def test_kmvm_square(K, n, d, nrhs, beta):
+    rng = np.random.Generator(np.random.PCG64(n + d))
+    X = rng.uniform(-2, 2, size=(n, d)).astype(np.float32)
+    V = rng.normal(size=(n, nrhs)).astype(np.float32)
+    sigma = 0.3 * np.sqrt(d)
+    ctx = K()
+    Q = ctx.kmvm(_t(X), _t(X), _t(V), sigma, beta).cpu().numpy()
+    ref = O.kmvm(X, V.astype(np.float64), sigma, beta)
+    assert _relcols(Q, ref).max() <= 1e-5
+
+
+def test_kmvm_rectangular_and_small_config(K):
+    p = synth.small()
+    rng = np.random.Generator(np.random.PCG64(5))
+    Xt = rng.uniform(0, 1, size=(333, 4)).astype(np.float32)
+    V = p.Y
+    ctx = K()
+    Q = ctx.kmvm(_t(Xt), _t(p.X), _t(V), p.sigma).cpu().numpy()
+    ref = O.kmvm_rect(Xt, p.X, V.astype(np.float64), p.sigma)
+    assert _relcols(Q, ref).max() <= 1e-5
+    Q2 = ctx.kmvm(_t(p.X), _t(p.X), _t(V), p.sigma, p.beta).cpu().numpy()
+    assert _relcols(Q2, O.kmvm(p.X, V, p.sigma, p.beta)).max() <= 1e-5
+
+
+def test_kmvm_full_size_sampled_rows(K):
+    p = synth.mixture()
+    ctx = K()
+    Q = ctx.kmvm(_t(p.X), _t(p.X), _t(p.Y), p.sigma, p.beta).cpu().numpy()
+    rows = np.random.Generator(np.random.PCG64(9)).choice(p.n, 256, replace=False)
+    ref = O.kmvm(p.X, p.Y.astype(np.float64), p.sigma, p.beta, rows=rows)
+    assert _relcols(Q[rows], ref).max() <= 1e-5
+
+
+def test_residual_hp_fp64(K):
+    p = synth.small(n=700)
+    rng = np.random.Generator(np.random.PCG64(3))
+    A = rng.normal(size=(p.n, 2))
+    Y = np.concatenate([p.Y, p.Y * 0.5], axis=1).astype(np.float32)
+    ctx = K()
+    R = ctx.residual_hp(_t(p.X), _t(Y), _t(A, torch.float64), p.sigma, p.beta).cpu().numpy()
+    ref = O.residual(p.X, A, Y, p.sigma, p.beta)
+    assert np.abs(R - ref).max() <= 1e-12 * np.abs(ref).max() + 1e-13
+
+
+# ------------------------------------------------------------------ Algorithm 1
+def test_omega_matches_oracle_generator(K):
+    ctx = K()
+    l, n, seed = 7, 1000, 123456789012345
+    Om = ctx.omega(seed, l, n).cpu().numpy()
+    ref = O.omega(seed, l, n)
+    np.testing.assert_allclose(Om, ref.T, rtol=0, atol=2e-5)
+
+
+def test_sketch_matches_oracle(K):
+    p = synth.small(n=600)
+    l = 25
+    ctx = K()
+    Y = ctx.sketch(_t(p.X), p.sigma, l, seed=11).cpu().numpy()
+    ref = O.sketch(p.X, p.sigma, O.omega(11, l, p.n))
+    assert _relcols(Y, ref).max() <= 1e-5
+
+
+def test_qrcp_pivots_on_shared_sketch(K):
+    p = synth.small(n=1500)
+    l, k = 40, 35
+    Y = O.sketch(p.X, p.sigma, O.omega(3, l, p.n)).astype(np.float32)
+    ctx = K()
+    piv, rd = ctx.qrcp(_t(Y), k)
+    piv, rd = piv.cpu().numpy(), rd.cpu().numpy()
+    ref_p, ref_n, gap = O.qrcp_greedy(Y.T.astype(np.float64), k)
+    # unique while the runner-up is far behind (FP32 vs FP64 decisions agree there)
+    upto = int(np.argmax(gap < 1e-3)) if np.any(gap < 1e-3) else k
+    assert upto >= 10
+    assert np.array_equal(piv[:upto], ref_p[:upto])
+    np.testing.assert_allclose(rd[:upto], ref_n[:upto], rtol=2e-3)
+    # the rest is a valid pivot sequence: distinct indices, non-increasing norms
+    assert len(set(piv.tolist())) == k
+    assert np.all(np.diff(rd) <= 1e-3 * rd[0])
+
+
+# ------------------------------------------------------------------ Algorithms 3-4
+def test_precond_apply_matches_oracle_with_shared_anchors(K):
+    p = synth.small(n=1200, k=60)
+    ctx = K()
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=5)
+    S = ctx.anchors().cpu().numpy()
+    assert len(S) == p.k
+    M = O.Nystrom(p.X, S, p.sigma, p.beta)
+    x = np.random.Generator(np.random.PCG64(2)).normal(size=(p.n, 2))
+    z = ctx.apply_precond(_t(x)).cpu().numpy()
+    ref = np.stack([M.apply(x[:, 0]), M.apply(x[:, 1])], axis=1)
+    assert _relcols(z, ref).max() <= 2e-3
+
+
+def test_anchor_quality_close_to_oracle(K):
+    p = synth.small(n=1000, k=50)
+    ctx = K()
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=5)
+    S = ctx.anchors().cpu().numpy()
+    Kfull = O.kernel_matrix(p.X, p.X, p.sigma)
+    err_gpu = np.linalg.norm(Kfull - O.Nystrom(p.X, S, p.sigma, p.beta).ktilde(), 2)
+    S_or = O.anchor_selection(p.X, p.sigma, p.k, p.l, seed=5)
+    err_or = np.linalg.norm(Kfull - O.Nystrom(p.X, S_or, p.sigma, p.beta).ktilde(), 2)
+    assert err_gpu <= 2.0 * err_or
+
+
+# ------------------------------------------------------------------ Algorithm 5
+def test_solve_small_config_vs_dense(K):
+    p = synth.small()
+    ctx = K()
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
+    alpha, info = ctx.solve(_t(p.Y), tol=p.tol)
+    a = alpha.cpu().numpy()
+    ref = O.solve_dense(p.X, p.Y.astype(np.float64), p.sigma, p.beta)
+    r = O.residual(p.X, a, p.Y, p.sigma, p.beta)
+    assert np.linalg.norm(r) / np.linalg.norm(p.Y) <= 1e-6
+    assert info["rel_residual"][0] <= 1e-6
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_solve_multi_rhs_and_predict(K):
+    p = synth.small(n=900, k=60)
+    rng = np.random.Generator(np.random.PCG64(8))
+    Y = np.concatenate([p.Y, rng.normal(size=(p.n, 2))], axis=1).astype(np.float32)
+    ctx = K()
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=2)
+    alpha, info = ctx.solve(_t(Y), tol=1e-6)
+    a = alpha.cpu().numpy()
+    ref = O.solve_dense(p.X, Y.astype(np.float64), p.sigma, p.beta)
+    assert _relcols(a, ref).max() <= 1e-4
+    Xt = rng.uniform(0, 1, size=(200, 4)).astype(np.float32)
+    f = ctx.predict(_t(Xt), alpha.float()).cpu().numpy()
+    fref = O.predict(Xt, p.X, a.astype(np.float32).astype(np.float64), p.sigma)
+    assert _relcols(f, fref).max() <= 1e-5
+
+
+def test_solve_full_size_mixture_sampled_residual(K):
+    p = synth.mixture()
+    ctx = K()
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
+    alpha, info = ctx.solve(_t(p.Y), tol=p.tol)
+    a = alpha.cpu().numpy()
+    rows = np.random.Generator(np.random.PCG64(4)).choice(p.n, 512, replace=False)
+    r = O.residual(p.X, a, p.Y, p.sigma, p.beta, rows=rows)
+    # sampled estimate of ||r|| / ||y||
+    assert np.linalg.norm(r) / np.linalg.norm(p.Y[rows]) <= 2e-6
+    assert info["rel_residual"][0] <= 1e-6
+
+
+# ------------------------------------------------------------------ edge cases
+def test_rank_deficient_points_drop_anchors(K):
+    base = np.random.Generator(np.random.PCG64(1)).uniform(0, 1, size=(12, 2))
+    X = np.repeat(base, 40, axis=0).astype(np.float32)
+    y = np.sin(X.sum(1)).astype(np.float32)
+    ctx = K()
+    ctx.build(_t(X), 0.3, 0.1, 30, seed=3)
+    S = ctx.anchors().cpu().numpy()
+    assert len(S) <= 12
+    alpha, info = ctx.solve(_t(y), tol=1e-8)
+    r = O.residual(X, alpha.cpu().numpy(), y, 0.3, 0.1)
+    assert np.linalg.norm(r) / np.linalg.norm(y) <= 1e-8
+
+
+def test_tiny_problem_k_equals_n(K):
+    X = np.array([[0.0], [1.0], [2.5]], dtype=np.float32)
+    y = np.array([1.0, -2.0, 0.5], dtype=np.float32)
+    ctx = K()
+    ctx.build(_t(X), 0.7, 0.05, 3, seed=0)
+    alpha, _ = ctx.solve(_t(y), tol=1e-10)
+    np.testing.assert_allclose(alpha.cpu().numpy(), O.solve_dense(X, y, 0.7, 0.05), rtol=1e-8)
+
+
+def test_bad_arguments_raise(K):
+    from paper_1905_10587_gb300.api import KRRError
+    ctx = K()
+    X = torch.zeros((10, 2), device="cuda")
+    with pytest.raises(KRRError):
+        ctx.build(X, -1.0, 0.1, 3)
+    with pytest.raises(KRRError):
+        ctx.build(X, 1.0, 0.0, 3)
+    with pytest.raises(KRRError):
+        ctx.build(X, 1.0, 0.1, 11)
+    with pytest.raises(KRRError):
+        ctx.solve(torch.zeros(10, device="cuda"))
+    with pytest.raises(KRRError):
+        ctx.kmvm(X, X[:5], torch.zeros(5, device="cuda"), 1.0, beta=0.1)
