@@ -61,7 +61,9 @@ typedef struct krr_opts {
     double inner_tol;     /* relative tolerance of each inner PCG solve (default 1e-4)   */
     double anchor_rtol;   /* pivots with |R_jj| < anchor_rtol |R_11| are dropped (1e-5)  */
     int    precision;     /* 0: FP32 kernel tiles (default); reserved for other modes   */
-    int    reserved[7];
+    int    residual;      /* refinement residual: 0 float-float on the FP32 pipe
+                             (default), 1 FP64 pipe                                      */
+    int    reserved[6];
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -121,6 +123,13 @@ int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long 
  * output R (n x nrhs each, RHS-major); K entries and sums carried in FP64 from
  * exact differences of the float32 coordinates.  Used for the refinement step. */
 int krr_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                    const float* Y, const double* A, int nrhs, double* R);
+
+/* The same residual with every quantity held as a float-float pair on the FP32 pipe
+ * (exact products and sums by error-free transformations, 2^t from a 2^(j/64)
+ * table and a degree-5 series); kernel values to a few 1e-12 relative.  For d > 16
+ * it falls back to the FP64 evaluation above. */
+int krr_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                     const float* Y, const double* A, int nrhs, double* R);
 
 /* ---------------------------------------------------------------------------

@@ -214,6 +214,28 @@ def qrcp_greedy(Yt: np.ndarray, k: int):
     return np.array(piv, dtype=np.int64), np.array(nrm), np.array(gap)
 
 
+def qrcp_replay(Yt: np.ndarray, piv: np.ndarray):
+    """Replay a given pivot sequence through the greedy rule of ``qrcp_greedy``.
+
+    Returns, per step, the residual norm of the given pivot and the largest
+    residual norm among the columns still available, so a caller can check
+    that each given choice was (within its own rounding) a maximal one.
+    """
+    A = np.array(Yt, dtype=np.float64, copy=True)
+    chosen = np.zeros(A.shape[1], dtype=bool)
+    got, best = [], []
+    for p in np.asarray(piv, dtype=np.int64):
+        s = np.einsum("ij,ij->j", A, A)
+        s[chosen] = -1.0
+        got.append(math.sqrt(max(s[p], 0.0)))
+        best.append(math.sqrt(max(s.max(), 0.0)))
+        chosen[p] = True
+        if s[p] > 0.0:
+            q = A[:, p] / math.sqrt(s[p])
+            A -= np.outer(q, q @ A)
+    return np.array(got), np.array(best)
+
+
 def anchor_selection(X: np.ndarray, sigma: float, k: int, l: int, seed: int):
     """Algorithm 1: Gaussian sketch, pivoted QR on Y^T, S = first k pivots."""
     Om = omega(seed, l, X.shape[0])

@@ -25,7 +25,7 @@ KRR_E_STATE, KRR_E_NOMEM, KRR_E_NONFINITE = 5, 6, 7
 class KrrOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("refine_max", C.c_int), ("oversample", C.c_int),
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
-                ("precision", C.c_int), ("reserved", C.c_int * 7)]
+                ("precision", C.c_int), ("residual", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class KrrSolveInfo(C.Structure):
@@ -48,6 +48,7 @@ SIGNATURES = {
     "krr_peak_probe": (_i, [_i, C.POINTER(_d), _vp]),
     "krr_kmvm": (_i, [_vp, _vp, _ll, _vp, _ll, _i, _d, _d, _vp, _i, _vp]),
     "krr_residual_hp": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _vp, _i, _vp]),
+    "krr_residual_ff": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _vp, _i, _vp]),
     "krr_omega": (_i, [_vp, _ull, _i, _ll, _vp]),
     "krr_sketch": (_i, [_vp, _vp, _ll, _i, _d, _i, _ull, _vp]),
     "krr_qrcp": (_i, [_vp, _vp, _ll, _i, _i, _vp, _vp]),

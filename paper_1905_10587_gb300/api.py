@@ -113,14 +113,15 @@ class KRR:
                                       Xr.shape[1], sigma, beta, _ptr(Vt), Vt.shape[0], _ptr(Q)))
         return _uncols(Q, vec)
 
-    def residual_hp(self, X, Y, A, sigma: float, beta: float) -> torch.Tensor:
-        """Y - (K + beta I) A in FP64 (A float64, Y float32)."""
+    def residual_hp(self, X, Y, A, sigma: float, beta: float, mode: str = "fp64") -> torch.Tensor:
+        """Y - (K + beta I) A in FP64 ("fp64") or float-float ("ff"); A float64, Y float32."""
         X = _cuda(X, torch.float32, "X")
         Yt, vec = _cols(Y, torch.float32, "Y")
         At, _ = _cols(A, torch.float64, "A")
         R = torch.empty_like(At)
-        self._check(self.lib.krr_residual_hp(self.h, _ptr(X), X.shape[0], X.shape[1], sigma, beta,
-                                             _ptr(Yt), _ptr(At), Yt.shape[0], _ptr(R)))
+        fn = self.lib.krr_residual_ff if mode == "ff" else self.lib.krr_residual_hp
+        self._check(fn(self.h, _ptr(X), X.shape[0], X.shape[1], sigma, beta,
+                       _ptr(Yt), _ptr(At), Yt.shape[0], _ptr(R)))
         return _uncols(R, vec)
 
     # ---------------------------------------------------------------- Algorithm 1

@@ -221,6 +221,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
     else krr_default_opts(&ctx->opts);
     if (ctx->opts.max_iter < 1 || ctx->opts.refine_max < 1 || ctx->opts.oversample < 0 ||
         ctx->opts.check_every < 1 || !(ctx->opts.inner_tol > 0.0) || ctx->opts.inner_tol >= 1.0 ||
+        ctx->opts.residual < 0 || ctx->opts.residual > 1 ||
         !(ctx->opts.anchor_rtol >= 0.0)) {
         delete ctx;
         return KRR_E_INVAL;
@@ -334,6 +335,16 @@ int krr_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sig
     if (!Y || !A || !R) return fail(ctx, KRR_E_INVAL, "null Y, A or R");
     if (nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "nrhs must be in [1, 16]");
     return launch_residual_hp(ctx, X, n, d, sigma, beta, Y, A, nrhs, R);
+}
+
+int krr_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                    const float* Y, const double* A, int nrhs, double* R) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, X, n, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, beta, false));
+    if (!Y || !A || !R) return fail(ctx, KRR_E_INVAL, "null Y, A or R");
+    if (nrhs < 1 || nrhs > KRR_MAX_RHS) return fail(ctx, KRR_E_INVAL, "nrhs must be in [1, 16]");
+    return launch_residual_ff(ctx, X, n, d, sigma, beta, Y, A, nrhs, R);
 }
 
 int krr_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, float* OmT) {
@@ -500,7 +511,6 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     std::memset(&inf, 0, sizeof(inf));
     inf.k_eff = ctx->k_eff;
     inf.build_ms = ctx->build_ms;
-    const double tol2_inner = ctx->opts.inner_tol * ctx->opts.inner_tol;
     int status = KRR_E_NOCONV;
     for (int sweep = 0;; ++sweep) {
         // residual of the current alpha (exactly y for alpha = 0)
@@ -510,8 +520,12 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         } else {
             {
                 Phase ph(ctx, PH_RESID);
-                KRR_RET(launch_residual_hp(ctx, ctx->X, n, ctx->d, ctx->sigma, ctx->beta, Y, alpha,
-                                           nrhs, r64));
+                if (ctx->opts.residual == 1)
+                    KRR_RET(launch_residual_hp(ctx, ctx->X, n, ctx->d, ctx->sigma, ctx->beta, Y,
+                                               alpha, nrhs, r64));
+                else
+                    KRR_RET(launch_residual_ff(ctx, ctx->X, n, ctx->d, ctx->sigma, ctx->beta, Y,
+                                               alpha, nrhs, r64));
             }
             KRR_RET(launch_dot64(ctx, r64, r64, n, nrhs, rnorm2));
             KRR_TRY_CUDA(cudaMemcpyAsync(rn.data(), rnorm2, sizeof(double) * nrhs,
@@ -519,12 +533,18 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
         }
         bool done = true;
+        double worst = 0.0;
         for (int c = 0; c < nrhs; ++c) {
             const double rel = yn[c] > 0.0 ? std::sqrt(rn[c] / yn[c]) : 0.0;
             inf.rel_residual[c] = rel;
             if (!std::isfinite(rel)) return fail(ctx, KRR_E_NONFINITE, "non-finite residual");
             if (rel > tol) done = false;
+            worst = std::max(worst, rel);
         }
+        // the inner solve only has to close the remaining gap (with a margin of 5),
+        // never asked for more than inner_tol: FP32 products cannot deliver much more
+        const double eta = std::min(0.5, std::max(ctx->opts.inner_tol, 0.2 * tol / worst));
+        const double tol2_inner = eta * eta;
         inf.sweeps = sweep;
         if (done) {
             status = KRR_OK;

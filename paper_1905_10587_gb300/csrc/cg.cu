@@ -88,51 +88,78 @@ int launch_dot64(krr_ctx* ctx, const double* A, const double* B, long long n, in
 }
 
 // ------------------------------------------------------------------ Woodbury apply
-// u_part[blk][q][a] = sum_{i in chunk(blk)} F[i, a] R[q, i]   (a < k, 8 columns per thread)
+constexpr int GT_ROWS = 256;   // rows of R staged in shared memory per batch
+
+// u_part[blk][q][a] = sum_{i in chunk(blk)} F[i, a] R[q, i].  Thread t owns the float4
+// columns 4t.. (stride 4*VT), so one CTA streams whole rows of F with 16-byte loads.
 template <int NQ>
 __global__ void __launch_bounds__(VT)
-k_gemv_t(const float* __restrict__ F, long long n, int k, int ldF, const float* __restrict__ R,
+k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restrict__ R,
          long long ldr, long long rows_per, float* __restrict__ upart) {
-    constexpr int KA = 8;
+    __shared__ float sr[NQ][GT_ROWS];
     const long long r0 = (long long)blockIdx.x * rows_per;
     const long long r1 = min(n, r0 + rows_per);
-    for (int a0 = 0; a0 < k; a0 += KA * VT) {
-        float acc[KA][NQ];
+    const int ld4 = ldF >> 2;
+    const float4* F4 = reinterpret_cast<const float4*>(F);
+    for (int c0 = 0; c0 < ld4; c0 += VT) {
+        const int c4 = c0 + threadIdx.x;
+        float4 acc[NQ];
 #pragma unroll
-        for (int m = 0; m < KA; ++m)
+        for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (long long b0 = r0; b0 < r1; b0 += GT_ROWS) {
+            const int nb = (int)min((long long)GT_ROWS, r1 - b0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < NQ * GT_ROWS; e += VT) {
+                const int q = e / GT_ROWS, i = e - q * GT_ROWS;
+                sr[q][i] = (i < nb) ? R[q * ldr + b0 + i] : 0.f;
+            }
+            __syncthreads();
+            if (c4 < ld4) {
+                const float4* fp = F4 + b0 * ld4 + c4;
+                int i = 0;
+                for (; i + 4 <= nb; i += 4) {
+                    const float4 f0 = fp[(size_t)(i + 0) * ld4];
+                    const float4 f1 = fp[(size_t)(i + 1) * ld4];
+                    const float4 f2 = fp[(size_t)(i + 2) * ld4];
+                    const float4 f3 = fp[(size_t)(i + 3) * ld4];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) acc[m][q] = 0.f;
-        for (long long i = r0; i < r1; ++i) {
-            float rv[NQ];
+                    for (int q = 0; q < NQ; ++q) {
+                        const float a0 = sr[q][i], a1 = sr[q][i + 1], a2 = sr[q][i + 2], a3 = sr[q][i + 3];
+                        acc[q].x = fmaf(f0.x, a0, fmaf(f1.x, a1, fmaf(f2.x, a2, fmaf(f3.x, a3, acc[q].x))));
+                        acc[q].y = fmaf(f0.y, a0, fmaf(f1.y, a1, fmaf(f2.y, a2, fmaf(f3.y, a3, acc[q].y))));
+                        acc[q].z = fmaf(f0.z, a0, fmaf(f1.z, a1, fmaf(f2.z, a2, fmaf(f3.z, a3, acc[q].z))));
+                        acc[q].w = fmaf(f0.w, a0, fmaf(f1.w, a1, fmaf(f2.w, a2, fmaf(f3.w, a3, acc[q].w))));
+                    }
+                }
+                for (; i < nb; ++i) {
+                    const float4 f = fp[(size_t)i * ld4];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) rv[q] = R[q * ldr + i];
-            const float* fr = F + i * ldF;
-#pragma unroll
-            for (int m = 0; m < KA; ++m) {
-                const int a = a0 + m * VT + threadIdx.x;
-                const float f = (a < k) ? fr[a] : 0.f;
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) acc[m][q] = fmaf(f, rv[q], acc[m][q]);
+                    for (int q = 0; q < NQ; ++q) {
+                        const float a = sr[q][i];
+                        acc[q].x = fmaf(f.x, a, acc[q].x);
+                        acc[q].y = fmaf(f.y, a, acc[q].y);
+                        acc[q].z = fmaf(f.z, a, acc[q].z);
+                        acc[q].w = fmaf(f.w, a, acc[q].w);
+                    }
+                }
             }
         }
+        if (c4 < ld4) {
 #pragma unroll
-        for (int m = 0; m < KA; ++m) {
-            const int a = a0 + m * VT + threadIdx.x;
-            if (a < k)
-#pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    upart[((size_t)blockIdx.x * NQ + q) * k + a] = acc[m][q];
+            for (int q = 0; q < NQ; ++q)
+                reinterpret_cast<float4*>(upart + ((size_t)blockIdx.x * NQ + q) * ldF)[c4] = acc[q];
         }
     }
 }
 
-// u[q][a] = sum_blk upart (FP64)
-__global__ void k_gemv_t_reduce(const float* __restrict__ upart, int nblk, int nq, int k,
+// u[q][a] = sum_blk upart (FP64), a < k
+__global__ void k_gemv_t_reduce(const float* __restrict__ upart, int nblk, int nq, int k, int ldF,
                                 double* __restrict__ u) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nq * k) return;
+    const int q = e / k, a = e - q * k;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += (double)upart[(size_t)b * nq * k + e];
+    for (int b = 0; b < nblk; ++b) s += (double)upart[((size_t)b * nq + q) * ldF + a];
     u[e] = s;
 }
 
@@ -151,16 +178,28 @@ __global__ void k_tri_gemv(const double* __restrict__ T, int k, const double* __
     }
 }
 
-// Z[q][i] = (R[q][i] - sum_a F[i, a] v[q][a]) / beta; one warp per row.  Optional partial R.Z.
+// Z[q][i] = (R[q][i] - sum_a F[i, a] v[q][a]) / beta; one warp per row with float4 loads.
+// Optional per-block partial sums of R.Z.
 template <int NQ>
 __global__ void __launch_bounds__(VT)
 k_gemv_n_apply(const float* __restrict__ F, long long n, int k, int ldF, const double* __restrict__ v,
                const float* __restrict__ R, long long ldr, float inv_beta, float* __restrict__ Z,
                double* __restrict__ rz_part) {
-    extern __shared__ float sv[];   // NQ x k
-    for (int e = threadIdx.x; e < NQ * k; e += VT) sv[e] = (float)v[e];
+    extern __shared__ float4 sv4[];   // NQ x ld4
+    const int ld4 = ldF >> 2;
+    for (int e = threadIdx.x; e < NQ * ld4; e += VT) {
+        const int q = e / ld4, c4 = e - q * ld4;
+        float t[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int a = 4 * c4 + w;
+            t[w] = (a < k) ? (float)v[(size_t)q * k + a] : 0.f;
+        }
+        sv4[e] = make_float4(t[0], t[1], t[2], t[3]);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float4* F4 = reinterpret_cast<const float4*>(F);
     double rz[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) rz[q] = 0.0;
@@ -168,11 +207,15 @@ k_gemv_n_apply(const float* __restrict__ F, long long n, int k, int ldF, const d
         float s[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) s[q] = 0.f;
-        const float* fr = F + i * ldF;
-        for (int a = lane; a < k; a += 32) {
-            const float f = fr[a];
+        const float4* fr = F4 + i * ld4;
+#pragma unroll 4
+        for (int c4 = lane; c4 < ld4; c4 += 32) {
+            const float4 f = fr[c4];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) s[q] = fmaf(f, sv[q * k + a], s[q]);
+            for (int q = 0; q < NQ; ++q) {
+                const float4 vv = sv4[q * ld4 + c4];
+                s[q] = fmaf(f.x, vv.x, fmaf(f.y, vv.y, fmaf(f.z, vv.z, fmaf(f.w, vv.w, s[q]))));
+            }
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -191,7 +234,7 @@ k_gemv_n_apply(const float* __restrict__ F, long long n, int k, int ldF, const d
     }
 }
 
-typedef void (*gemv_t_fn)(const float*, long long, int, int, const float*, long long, long long, float*);
+typedef void (*gemv_t_fn)(const float*, long long, int, const float*, long long, long long, float*);
 typedef void (*gemv_n_fn)(const float*, long long, int, int, const double*, const float*, long long,
                           float, float*, double*);
 
@@ -199,12 +242,12 @@ typedef void (*gemv_n_fn)(const float*, long long, int, int, const double*, cons
 // sums of R.Z laid out [q][blk] with vec_blocks(n) blocks per column.
 int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part) {
     const long long n = ctx->n;
-    const int k = ctx->k_eff;
+    const int k = ctx->k_eff, ldF = ctx->ldF;
     const int nb = vec_blocks(ctx, n);
     const long long rows_per = ceil_div(n, nb);
     float* upart;
     double *u, *u1, *v;
-    KRR_RET(bufT(ctx, "ap_upart", (size_t)nb * 4 * k, &upart));
+    KRR_RET(bufT(ctx, "ap_upart", (size_t)nb * 4 * ldF, &upart));
     KRR_RET(bufT(ctx, "ap_u", (size_t)4 * k, &u));
     KRR_RET(bufT(ctx, "ap_u1", (size_t)4 * k, &u1));
     KRR_RET(bufT(ctx, "ap_v", (size_t)4 * k, &v));
@@ -216,20 +259,20 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
                      : nq == 3 ? &k_gemv_n_apply<3> : &k_gemv_n_apply<4>;
         const float* Rq = R + (size_t)q0 * n;
         float* Zq = Z + (size_t)q0 * n;
-        gt<<<nb, VT, 0, ctx->stream>>>(ctx->F, n, k, ctx->ldF, Rq, n, rows_per, upart);
+        gt<<<nb, VT, 0, ctx->stream>>>(ctx->F, n, ldF, Rq, n, rows_per, upart);
         KRR_CHECK_LAUNCH();
-        k_gemv_t_reduce<<<ceil_div((long long)nq * k, 256), 256, 0, ctx->stream>>>(upart, nb, nq, k, u);
+        k_gemv_t_reduce<<<ceil_div((long long)nq * k, 256), 256, 0, ctx->stream>>>(upart, nb, nq, k, ldF, u);
         KRR_CHECK_LAUNCH();
         k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2, k, u, nq, true, u1);
         KRR_CHECK_LAUNCH();
         k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2t, k, u1, nq, false, v);
         KRR_CHECK_LAUNCH();
-        const size_t smem = sizeof(float) * nq * k;
+        const size_t smem = sizeof(float4) * nq * (ldF / 4);
         if (smem > 48 * 1024) {
             KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)gn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         }
-        gn<<<nb, VT, smem, ctx->stream>>>(ctx->F, n, k, ctx->ldF, v, Rq, n, inv_beta, Zq,
+        gn<<<nb, VT, smem, ctx->stream>>>(ctx->F, n, k, ldF, v, Rq, n, inv_beta, Zq,
                                           rz_part ? rz_part + (size_t)q0 * nb : nullptr);
         KRR_CHECK_LAUNCH();
     }

@@ -172,6 +172,10 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
 int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);
 
+// residual_ff.cu: same contract in float-float on the FP32 pipe (d <= 16; else FP64)
+int launch_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
+                       const float* Y, const double* A, int nrhs, double* R);
+
 // sketch.cu
 int launch_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, int ld, float* OmT);
 // Out[i*ldo + a] = sum_j K(Pr_i, Pc_j) V[j*ldv + a], a < ncol (FP32 SIMT contraction)

@@ -225,7 +225,7 @@ __global__ void k_kmvm_reduce(const float* __restrict__ part, int splits, int nr
 
 template <int D, int NRHS>
 constexpr int kmvm_rows() {
-    return (D > 32) ? 1 : (D > 16 || (NRHS >= 8 && D >= 8)) ? 2 : 4;
+    return (D > 32) ? 1 : (D > 16 || NRHS >= 16 || (NRHS >= 8 && D >= 8)) ? 2 : 4;
 }
 
 typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float,
@@ -289,6 +289,8 @@ static int choose_splits(int nblk, int ntiles, int slots) {
     }
     return best;
 }
+
+int choose_splits_public(int nblk, int ntiles, int slots) { return choose_splits(nblk, ntiles, slots); }
 
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
                 float beta, const float* V, int nrhs, float* Q) {

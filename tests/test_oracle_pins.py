@@ -151,6 +151,20 @@ def test_qrcp_matches_greedy_rule():
     np.testing.assert_allclose(rd[:upto], nrm[:upto], rtol=1e-10)
 
 
+def test_qrcp_replay_of_greedy_pivots_is_maximal():
+    rng = np.random.Generator(np.random.PCG64(17))
+    A = rng.normal(size=(9, 40))
+    piv, nrm, _ = O.qrcp_greedy(A, 8)
+    got, best = O.qrcp_replay(A, piv)
+    np.testing.assert_allclose(got, best, rtol=1e-12)
+    np.testing.assert_allclose(got, nrm, rtol=1e-12)
+    # a non-greedy sequence is caught
+    bad = piv.copy()
+    bad[2], bad[5] = bad[5], bad[2]
+    g2, b2 = O.qrcp_replay(A, bad)
+    assert g2[2] < b2[2] * (1 - 1e-6)
+
+
 def test_qrcp_picks_largest_then_orthogonal():
     # columns e1*5, e1*4 (parallel to the first), e2*3: pivots 0 then 2
     A = np.array([[5.0, 4.0, 0.0], [0.0, 0.0, 3.0]])
