@@ -90,12 +90,29 @@ int launch_dot64(krr_ctx* ctx, const double* A, const double* B, long long n, in
 // ------------------------------------------------------------------ Woodbury apply
 constexpr int GT_ROWS = 256;   // rows of R staged in shared memory per batch
 
-// u_part[blk][q][a] = sum_{i in chunk(blk)} F[i, a] R[q, i].  Thread t owns the float4
-// columns 4t.. (stride 4*VT), so one CTA streams whole rows of F with 16-byte loads.
+// Error-free transformations (Knuth two-sum, FMA two-product) for compensated sums.
+__device__ __forceinline__ void cg_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+__device__ __forceinline__ void ff_acc(float& h, float& l, float f, float r) {
+    const float p = __fmul_rn(f, r);
+    const float pe = fmaf(f, r, -p);
+    float s, e;
+    cg_two_sum(h, p, s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, pe));
+}
+
+// u_part[blk][q][a] = sum_{i in chunk(blk)} F[i, a] R[q, i], as FP64.  Thread t owns the
+// float4 columns 4t.. (stride 4*VT), so one CTA streams whole rows of F with 16-byte
+// loads.  Products are exact and the sums compensated (float-float): F^T r carries the
+// cancellation of the preconditioner, and a plain FP32 sum costs PCG iterations.
 template <int NQ>
 __global__ void __launch_bounds__(VT)
 k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restrict__ R,
-         long long ldr, long long rows_per, float* __restrict__ upart) {
+         long long ldr, long long rows_per, double* __restrict__ upart) {
     __shared__ float sr[NQ][GT_ROWS];
     const long long r0 = (long long)blockIdx.x * rows_per;
     const long long r1 = min(n, r0 + rows_per);
@@ -103,9 +120,9 @@ k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restr
     const float4* F4 = reinterpret_cast<const float4*>(F);
     for (int c0 = 0; c0 < ld4; c0 += VT) {
         const int c4 = c0 + threadIdx.x;
-        float4 acc[NQ];
+        float hx[NQ], hy[NQ], hz[NQ], hw[NQ], lx[NQ], ly[NQ], lz[NQ], lw[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < NQ; ++q) hx[q] = hy[q] = hz[q] = hw[q] = lx[q] = ly[q] = lz[q] = lw[q] = 0.f;
         for (long long b0 = r0; b0 < r1; b0 += GT_ROWS) {
             const int nb = (int)min((long long)GT_ROWS, r1 - b0);
             __syncthreads();
@@ -117,18 +134,16 @@ k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restr
             if (c4 < ld4) {
                 const float4* fp = F4 + b0 * ld4 + c4;
                 int i = 0;
-                for (; i + 4 <= nb; i += 4) {
+                for (; i + 2 <= nb; i += 2) {
                     const float4 f0 = fp[(size_t)(i + 0) * ld4];
                     const float4 f1 = fp[(size_t)(i + 1) * ld4];
-                    const float4 f2 = fp[(size_t)(i + 2) * ld4];
-                    const float4 f3 = fp[(size_t)(i + 3) * ld4];
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
-                        const float a0 = sr[q][i], a1 = sr[q][i + 1], a2 = sr[q][i + 2], a3 = sr[q][i + 3];
-                        acc[q].x = fmaf(f0.x, a0, fmaf(f1.x, a1, fmaf(f2.x, a2, fmaf(f3.x, a3, acc[q].x))));
-                        acc[q].y = fmaf(f0.y, a0, fmaf(f1.y, a1, fmaf(f2.y, a2, fmaf(f3.y, a3, acc[q].y))));
-                        acc[q].z = fmaf(f0.z, a0, fmaf(f1.z, a1, fmaf(f2.z, a2, fmaf(f3.z, a3, acc[q].z))));
-                        acc[q].w = fmaf(f0.w, a0, fmaf(f1.w, a1, fmaf(f2.w, a2, fmaf(f3.w, a3, acc[q].w))));
+                        const float a0 = sr[q][i], a1 = sr[q][i + 1];
+                        ff_acc(hx[q], lx[q], f0.x, a0); ff_acc(hy[q], ly[q], f0.y, a0);
+                        ff_acc(hz[q], lz[q], f0.z, a0); ff_acc(hw[q], lw[q], f0.w, a0);
+                        ff_acc(hx[q], lx[q], f1.x, a1); ff_acc(hy[q], ly[q], f1.y, a1);
+                        ff_acc(hz[q], lz[q], f1.z, a1); ff_acc(hw[q], lw[q], f1.w, a1);
                     }
                 }
                 for (; i < nb; ++i) {
@@ -136,30 +151,33 @@ k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restr
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
                         const float a = sr[q][i];
-                        acc[q].x = fmaf(f.x, a, acc[q].x);
-                        acc[q].y = fmaf(f.y, a, acc[q].y);
-                        acc[q].z = fmaf(f.z, a, acc[q].z);
-                        acc[q].w = fmaf(f.w, a, acc[q].w);
+                        ff_acc(hx[q], lx[q], f.x, a); ff_acc(hy[q], ly[q], f.y, a);
+                        ff_acc(hz[q], lz[q], f.z, a); ff_acc(hw[q], lw[q], f.w, a);
                     }
                 }
             }
         }
         if (c4 < ld4) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q)
-                reinterpret_cast<float4*>(upart + ((size_t)blockIdx.x * NQ + q) * ldF)[c4] = acc[q];
+            for (int q = 0; q < NQ; ++q) {
+                double* o = upart + ((size_t)blockIdx.x * NQ + q) * ldF + 4 * c4;
+                o[0] = (double)hx[q] + (double)lx[q];
+                o[1] = (double)hy[q] + (double)ly[q];
+                o[2] = (double)hz[q] + (double)lz[q];
+                o[3] = (double)hw[q] + (double)lw[q];
+            }
         }
     }
 }
 
 // u[q][a] = sum_blk upart (FP64), a < k
-__global__ void k_gemv_t_reduce(const float* __restrict__ upart, int nblk, int nq, int k, int ldF,
+__global__ void k_gemv_t_reduce(const double* __restrict__ upart, int nblk, int nq, int k, int ldF,
                                 double* __restrict__ u) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nq * k) return;
     const int q = e / k, a = e - q * k;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += (double)upart[((size_t)b * nq + q) * ldF + a];
+    for (int b = 0; b < nblk; ++b) s += upart[((size_t)b * nq + q) * ldF + a];
     u[e] = s;
 }
 
@@ -234,7 +252,7 @@ k_gemv_n_apply(const float* __restrict__ F, long long n, int k, int ldF, const d
     }
 }
 
-typedef void (*gemv_t_fn)(const float*, long long, int, const float*, long long, long long, float*);
+typedef void (*gemv_t_fn)(const float*, long long, int, const float*, long long, long long, double*);
 typedef void (*gemv_n_fn)(const float*, long long, int, int, const double*, const float*, long long,
                           float, float*, double*);
 
@@ -245,8 +263,7 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
     const int k = ctx->k_eff, ldF = ctx->ldF;
     const int nb = vec_blocks(ctx, n);
     const long long rows_per = ceil_div(n, nb);
-    float* upart;
-    double *u, *u1, *v;
+    double *upart, *u, *u1, *v;
     KRR_RET(bufT(ctx, "ap_upart", (size_t)nb * 4 * ldF, &upart));
     KRR_RET(bufT(ctx, "ap_u", (size_t)4 * k, &u));
     KRR_RET(bufT(ctx, "ap_u1", (size_t)4 * k, &u1));

@@ -233,6 +233,22 @@ def test_solve_full_size_mixture_sampled_residual(K):
     assert info["rel_residual"][0] <= 1e-6
 
 
+def test_pcg_iterations_match_fp64_oracle(K):
+    # one sweep to 1e-4: the FP32 path must converge about as fast as the FP64 PCG of
+    # Algorithm 5 with the same anchors (an inexact preconditioner shows up here first)
+    p = synth.mixture(n=5000, k=500)
+    ctx = K(inner_tol=1e-4)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
+    S = ctx.anchors().cpu().numpy()
+    alpha, info = ctx.solve(_t(p.Y), tol=1e-4)
+    assert info["sweeps"] == 1
+    A = O.kernel_matrix(p.X, p.X, p.sigma) + p.beta * np.eye(p.n)
+    M = O.Nystrom(p.X, S, p.sigma, p.beta)
+    _, it = O.pcg(lambda v: A @ v, p.Y[:, 0].astype(np.float64), M.apply, tol=1e-4,
+                  replace_every=10 ** 9)
+    assert info["iters"] <= int(1.2 * it) + 2
+
+
 # ------------------------------------------------------------------ edge cases
 def test_rank_deficient_points_drop_anchors(K):
     base = np.random.Generator(np.random.PCG64(1)).uniform(0, 1, size=(12, 2))
