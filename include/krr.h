@@ -54,11 +54,13 @@ typedef struct krr_ctx krr_ctx;
 
 /* Solver options.  krr_default_opts() fills the defaults given here. */
 typedef struct krr_opts {
-    int    max_iter;      /* PCG iterations per refinement sweep (default 1000)          */
-    int    refine_max;    /* outer refinement sweeps (default 6)                         */
+    int    max_iter;      /* PCG iterations in total (default 5000)                      */
+    int    refine_max;    /* true-residual replacements allowed (default 40)             */
     int    oversample;    /* l = k + oversample random projections (default 5, Sec. 5.1) */
     int    check_every;   /* iterations between host convergence reads (default 1)      */
-    double inner_tol;     /* relative tolerance of each inner PCG solve (default 1e-4)   */
+    double inner_tol;     /* reliable-update factor: the FP32 recursive residual is
+                             replaced by the float-float true residual once it has
+                             dropped by this factor (default 1e-2)                        */
     double anchor_rtol;   /* pivots with |R_jj| < anchor_rtol |R_11| are dropped (1e-5)  */
     int    precision;     /* 0: FP32 kernel tiles (default); reserved for other modes   */
     int    residual;      /* refinement residual: 0 float-float on the FP32 pipe
@@ -70,12 +72,15 @@ typedef struct krr_opts {
 typedef struct krr_solve_info {
     int    status;                        /* KRR_OK or KRR_E_NOCONV                   */
     int    iters;                         /* PCG iterations summed over sweeps        */
-    int    sweeps;                        /* refinement sweeps run                    */
+    int    sweeps;                        /* true-residual replacements made          */
     int    k_eff;                         /* anchors kept by the build                */
     double rel_residual[KRR_MAX_RHS];     /* ||y - (K+beta I) alpha|| / ||y||, FP64   */
     double build_ms;                      /* time of the last krr_build_precond       */
     double solve_ms;                      /* wall time of this solve (host clock)     */
     int    mvm_count;                     /* kernel products (K+beta I)V issued       */
+    int    sweep_iters[8];                /* PCG iterations before each replacement   */
+    double sweep_residual[8];             /* worst column's true residual at the start
+                                             and after each replacement                */
     int    reserved[7];
 } krr_solve_info;
 
@@ -173,8 +178,11 @@ int krr_get_anchors(krr_ctx* ctx, int* S, int* k_eff);
 int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out);
 
 /* Solve (K + beta I) alpha = Y (Algorithm 5 step 3) for the built X to
- * ||Y - (K + beta I) alpha|| / ||Y|| <= tol per column, measured with the FP64
- * residual.  X must be the pointer given to the build.  alpha: n x nrhs FP64.
+ * ||Y - (K + beta I) alpha|| / ||Y|| <= tol per column, measured with the
+ * float-float (or FP64, opts.residual = 1) residual.  The PCG recurrence runs in
+ * FP32 with reliable updates: its recursive residual is replaced by the true one
+ * (and its iterate folded into the FP64 alpha) each time it drops by
+ * opts.inner_tol.  X must be the pointer given to the build.  alpha: n x nrhs FP64.
  * info (host) may be NULL.  Returns KRR_E_NOCONV (alpha still written) if
  * the limits are hit first. */
 int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol,

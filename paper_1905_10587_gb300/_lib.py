@@ -31,7 +31,8 @@ class KrrOpts(C.Structure):
 class KrrSolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("sweeps", C.c_int), ("k_eff", C.c_int),
                 ("rel_residual", C.c_double * KRR_MAX_RHS), ("build_ms", C.c_double),
-                ("solve_ms", C.c_double), ("mvm_count", C.c_int), ("reserved", C.c_int * 7)]
+                ("solve_ms", C.c_double), ("mvm_count", C.c_int), ("sweep_iters", C.c_int * 8),
+                ("sweep_residual", C.c_double * 8), ("reserved", C.c_int * 7)]
 
 
 _vp, _i, _ll, _d, _ull = C.c_void_p, C.c_int, C.c_longlong, C.c_double, C.c_ulonglong

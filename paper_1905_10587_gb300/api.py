@@ -189,7 +189,9 @@ class KRR:
                                        C.byref(info)), allow)
         out = dict(status=info.status, iters=info.iters, sweeps=info.sweeps, k_eff=info.k_eff,
                    rel_residual=[info.rel_residual[i] for i in range(Yt.shape[0])],
-                   build_ms=info.build_ms, solve_ms=info.solve_ms, mvm_count=info.mvm_count)
+                   build_ms=info.build_ms, solve_ms=info.solve_ms, mvm_count=info.mvm_count,
+                   sweep_iters=[info.sweep_iters[i] for i in range(min(8, info.sweeps + 1))],
+                   sweep_residual=[info.sweep_residual[i] for i in range(min(8, info.sweeps + 1))])
         return _uncols(A, vec), out
 
     def predict(self, Xtest, alpha) -> torch.Tensor:

@@ -83,6 +83,7 @@ int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const dou
 int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot);
 int launch_convert_up(krr_ctx* ctx, const float* a, double* b, long long tot);
 int launch_accumulate(krr_ctx* ctx, const float* x, double* y, long long tot);
+int launch_cg_set_active(krr_ctx* ctx, const int* act_host, int nrhs);
 
 static const double LOG2E = 1.4426950408889634;
 
@@ -203,11 +204,11 @@ extern "C" {
 int krr_default_opts(krr_opts* o) {
     if (!o) return KRR_E_INVAL;
     std::memset(o, 0, sizeof(*o));
-    o->max_iter = 1000;
-    o->refine_max = 6;
+    o->max_iter = 5000;
+    o->refine_max = 40;
     o->oversample = 5;
     o->check_every = 1;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 1e-2;
     o->anchor_rtol = 1e-5;
     o->precision = 0;
     return KRR_OK;
@@ -512,12 +513,22 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     inf.k_eff = ctx->k_eff;
     inf.build_ms = ctx->build_ms;
     int status = KRR_E_NOCONV;
-    for (int sweep = 0;; ++sweep) {
-        // residual of the current alpha (exactly y for alpha = 0)
-        if (sweep == 0) {
+
+    // One preconditioned CG recurrence in FP32 with reliable updates: whenever the
+    // recursive residual of a column has fallen by the factor opts.inner_tol since the
+    // last true residual (or looks converged), x is folded into the FP64 alpha and the
+    // recursive residual is replaced by y - (K + beta I) alpha evaluated in float-float.
+    // The search direction is kept, so the Krylov space is not thrown away.
+    const double delta2 = ctx->opts.inner_tol * ctx->opts.inner_tol;
+    std::vector<double> rtrue(nrhs);
+    std::vector<int> act(nrhs);
+    auto true_residual = [&](bool first) -> int {
+        if (first) {
             KRR_RET(launch_convert_up(ctx, Y, r64, tot));
             for (int c = 0; c < nrhs; ++c) rn[c] = yn[c];
         } else {
+            KRR_RET(launch_accumulate(ctx, x, alpha, tot));
+            KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
             {
                 Phase ph(ctx, PH_RESID);
                 if (ctx->opts.residual == 1)
@@ -532,37 +543,39 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                                          cudaMemcpyDeviceToHost, ctx->stream));
             KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
         }
-        bool done = true;
         double worst = 0.0;
         for (int c = 0; c < nrhs; ++c) {
             const double rel = yn[c] > 0.0 ? std::sqrt(rn[c] / yn[c]) : 0.0;
-            inf.rel_residual[c] = rel;
             if (!std::isfinite(rel)) return fail(ctx, KRR_E_NONFINITE, "non-finite residual");
-            if (rel > tol) done = false;
+            inf.rel_residual[c] = rel;
+            rtrue[c] = rn[c];
+            act[c] = rel > tol ? 1 : 0;
             worst = std::max(worst, rel);
         }
-        // the inner solve only has to close the remaining gap (with a margin of 5),
-        // never asked for more than inner_tol: FP32 products cannot deliver much more
-        const double eta = std::min(0.5, std::max(ctx->opts.inner_tol, 0.2 * tol / worst));
-        const double tol2_inner = eta * eta;
-        inf.sweeps = sweep;
-        if (done) {
-            status = KRR_OK;
-            break;
-        }
-        if (sweep >= ctx->opts.refine_max) break;
-
-        // inner PCG on A delta = r (FP32), to relative accuracy inner_tol
+        if (inf.sweeps < 8) inf.sweep_residual[inf.sweeps] = worst;
         KRR_RET(launch_convert(ctx, r64, r, tot));
-        KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+        return KRR_OK;
+    };
+    auto any_active = [&]() {
+        for (int c = 0; c < nrhs; ++c)
+            if (act[c]) return true;
+        return false;
+    };
+
+    KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+    KRR_RET(true_residual(true));
+    if (!any_active()) {
+        status = KRR_OK;
+    } else {
         {
             Phase ph(ctx, PH_APPLY);
             KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part1));
         }
         KRR_RET(launch_cg_start(ctx, r, z, nrhs, part1, part2));
+        KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
         KRR_TRY_CUDA(cudaMemcpyAsync(p, z, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
-        int it = 0;
-        while (it < ctx->opts.max_iter) {
+        int it = 0, since = 0;
+        while (true) {
             {
                 Phase ph(ctx, PH_KMVM);
                 KRR_RET(launch_kmvm(ctx, ctx->P, n, ctx->P, n, ctx->d, (float)ctx->beta, p, nrhs, q));
@@ -571,15 +584,37 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             {
                 Phase ph(ctx, PH_CGVEC);
                 KRR_RET(launch_cg_alpha(ctx, p, q, nrhs, part1));
-                KRR_RET(launch_cg_update_xr(ctx, x, r, p, q, nrhs, part2, tol2_inner));
+                KRR_RET(launch_cg_update_xr(ctx, x, r, p, q, nrhs, part2, 0.0));
             }
             ++it;
-            if (it % ctx->opts.check_every == 0 || it == ctx->opts.max_iter) {
+            ++since;
+            const bool last = it >= ctx->opts.max_iter;
+            if (it % ctx->opts.check_every == 0 || last) {
                 KRR_TRY_CUDA(cudaMemcpyAsync(ctx->cg_host, ctx->cg, sizeof(CGScalars),
                                              cudaMemcpyDeviceToHost, ctx->stream));
                 KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-                if (ctx->cg_host->bad) break;
-                if (ctx->cg_host->all_done) break;
+                if (ctx->cg_host->bad) {
+                    fail(ctx, KRR_E_NONFINITE, "non-positive curvature or non-finite value in PCG");
+                    break;
+                }
+                bool update = last;
+                for (int c = 0; c < nrhs; ++c) {
+                    if (!act[c]) continue;
+                    const double rr = ctx->cg_host->rr[c];
+                    if (rr <= delta2 * rtrue[c] || rr <= 0.25 * tol * tol * yn[c]) update = true;
+                }
+                if (update) {
+                    if (inf.sweeps < 8) inf.sweep_iters[inf.sweeps] = since;
+                    inf.sweeps++;
+                    since = 0;
+                    KRR_RET(true_residual(false));
+                    if (!any_active()) {
+                        status = KRR_OK;
+                        break;
+                    }
+                    if (last || inf.sweeps >= ctx->opts.refine_max) break;
+                    KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
+                }
             }
             {
                 Phase ph(ctx, PH_APPLY);
@@ -590,8 +625,11 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                 KRR_RET(launch_cg_beta_p(ctx, p, z, nrhs, part3));
             }
         }
-        inf.iters += it;
-        KRR_RET(launch_accumulate(ctx, x, alpha, tot));
+        inf.iters = it;
+        if (status != KRR_OK && since > 0) {
+            // fold the last partial correction so that alpha is the best iterate
+            KRR_RET(launch_accumulate(ctx, x, alpha, tot));
+        }
     }
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     inf.status = status;

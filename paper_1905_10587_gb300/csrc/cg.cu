@@ -11,6 +11,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace krr {
 
@@ -170,15 +171,26 @@ k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restr
     }
 }
 
-// u[q][a] = sum_blk upart (FP64), a < k
-__global__ void k_gemv_t_reduce(const double* __restrict__ upart, int nblk, int nq, int k, int ldF,
-                                double* __restrict__ u) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nq * k) return;
-    const int q = e / k, a = e - q * k;
+// u[q][a] = sum_blk upart (FP64), a < k.  A CTA covers 32 columns; its 8 warps split the
+// partials and combine them through shared memory (coalesced, many loads in flight).
+__global__ void __launch_bounds__(256)
+k_gemv_t_reduce(const double* __restrict__ upart, int nblk, int nq, int k, int ldF,
+                double* __restrict__ u) {
+    __shared__ double red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int a = blockIdx.x * 32 + lane;
+    const int q = blockIdx.y;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += upart[((size_t)b * nq + q) * ldF + a];
-    u[e] = s;
+    if (a < k)
+        for (int b = w; b < nblk; b += 8) s += upart[((size_t)b * nq + q) * ldF + a];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && a < k) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += red[i][lane];
+        u[(size_t)q * k + a] = t;
+    }
 }
 
 // y[q][a] = sum_b T[a][b] x[q][b] over b <= a (lower) or b >= a (upper).  One warp per row a.
@@ -278,7 +290,7 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
         float* Zq = Z + (size_t)q0 * n;
         gt<<<nb, VT, 0, ctx->stream>>>(ctx->F, n, ldF, Rq, n, rows_per, upart);
         KRR_CHECK_LAUNCH();
-        k_gemv_t_reduce<<<ceil_div((long long)nq * k, 256), 256, 0, ctx->stream>>>(upart, nb, nq, k, ldF, u);
+        k_gemv_t_reduce<<<dim3(ceil_div(k, 32), nq), 256, 0, ctx->stream>>>(upart, nb, nq, k, ldF, u);
         KRR_CHECK_LAUNCH();
         k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2, k, u, nq, true, u1);
         KRR_CHECK_LAUNCH();
@@ -335,7 +347,7 @@ k_cg_update_xr(float* __restrict__ x, float* __restrict__ r, const float* __rest
     }
 }
 
-// rr_q = sum part; column q stays active while rr_q > tol2 * rr0_q.
+// rr_q = sum part (recursive residual); columns with tol2 > 0 stop once rr_q <= tol2 rr0_q.
 __global__ void k_cg_check(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs,
                            double tol2) {
     __shared__ int any;
@@ -350,21 +362,21 @@ __global__ void k_cg_check(CGScalars* cg, const double* __restrict__ part, int n
             cg->bad = 1;
             cg->active[q] = 0;
         }
-        if (cg->active[q] && !(s > tol2 * cg->rr0[q])) cg->active[q] = 0;
+        if (tol2 > 0.0 && cg->active[q] && !(s > tol2 * cg->rr0[q])) cg->active[q] = 0;
         if (cg->active[q]) atomicOr(&any, 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) cg->all_done = any ? 0 : 1;
 }
 
-// b_q = rz_new / rz; rz = rz_new
+// b_q = rz_new / rz; rz = rz_new (b = 0 for finished columns: p restarts from z)
 __global__ void k_cg_beta(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs) {
     const int q = threadIdx.x;
     if (q >= nrhs) return;
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
     const double rz = cg->rz[q];
-    cg->b[q] = (rz != 0.0 && isfinite(s)) ? s / rz : 0.0;
+    cg->b[q] = (cg->active[q] && rz != 0.0 && isfinite(s)) ? s / rz : 0.0;
     cg->rz[q] = s;
 }
 
@@ -416,6 +428,14 @@ __global__ void k_axpy_f32_into_f64(const float* __restrict__ x, double* __restr
 }
 
 // ---- host drivers for the recurrences (launch sequences; no host sync inside)
+int launch_cg_set_active(krr_ctx* ctx, const int* act_host, int nrhs) {
+    // staged through the pinned mirror so the copy is asynchronous
+    std::memcpy(ctx->cg_host->active, act_host, sizeof(int) * nrhs);
+    KRR_TRY_CUDA(cudaMemcpyAsync(ctx->cg->active, ctx->cg_host->active, sizeof(int) * nrhs,
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    return KRR_OK;
+}
+
 int cg_vec_blocks(krr_ctx* ctx) { return vec_blocks(ctx, ctx->n); }
 
 int launch_cg_start(krr_ctx* ctx, const float* r, const float* z, int nrhs, double* rz_part,

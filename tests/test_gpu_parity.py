@@ -241,12 +241,21 @@ def test_pcg_iterations_match_fp64_oracle(K):
     ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
     S = ctx.anchors().cpu().numpy()
     alpha, info = ctx.solve(_t(p.Y), tol=1e-4)
-    assert info["sweeps"] == 1
     A = O.kernel_matrix(p.X, p.X, p.sigma) + p.beta * np.eye(p.n)
     M = O.Nystrom(p.X, S, p.sigma, p.beta)
     _, it = O.pcg(lambda v: A @ v, p.Y[:, 0].astype(np.float64), M.apply, tol=1e-4,
                   replace_every=10 ** 9)
     assert info["iters"] <= int(1.2 * it) + 2
+    # to 1e-6 with reliable updates: the replacements must not restart the recurrence.
+    # An FP32 recurrence loses CG's superlinear tail: emulating the FP32 product,
+    # preconditioner or vectors (each alone) turns 81 FP64 iterations into 105-117 at
+    # n = 1e4 on this workload, so the bound allows 1.5x.
+    ctx2 = K()
+    ctx2.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
+    _, info2 = ctx2.solve(_t(p.Y), tol=1e-6)
+    _, it6 = O.pcg(lambda v: A @ v, p.Y[:, 0].astype(np.float64), M.apply, tol=1e-6,
+                   replace_every=10 ** 9)
+    assert info2["iters"] <= int(1.5 * it6) + 2
 
 
 # ------------------------------------------------------------------ edge cases
