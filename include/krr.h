@@ -62,7 +62,9 @@ typedef struct krr_opts {
                              replaced by the float-float true residual once it has
                              dropped by this factor (default 1e-2)                        */
     double anchor_rtol;   /* pivots with |R_jj| < anchor_rtol |R_11| are dropped (1e-5)  */
-    int    precision;     /* 0: FP32 kernel tiles (default); reserved for other modes   */
+    int    precision;     /* kernel product of the PCG iterations: 0 = FP32 FFMA tiles
+                             (default); 1 = tcgen05 tensor cores, exponent from a BF16x3
+                             split GEMM (d <= 16; larger d uses the FP32 tiles)          */
     int    residual;      /* refinement residual: 0 float-float on the FP32 pipe
                              (default), 1 FP64 pipe                                      */
     int    reserved[6];
@@ -107,6 +109,14 @@ long long krr_launch_count(const krr_ctx* ctx);
  * occurrences (host outputs; synchronises on the recorded events). */
 int krr_profile_enable(krr_ctx* ctx, int on);
 int krr_profile_read(krr_ctx* ctx, const char* phase, double* total_ms, long long* count);
+
+/* Known-answer test of the tensor-core path's shared-memory and instruction
+ * descriptors: one 128 x 32 x 16 BF16 tcgen05.mma of small integers, compared on
+ * the host.  variant 0 is the layout the library uses (core matrices adjacent
+ * along K 128 bytes apart), variant 1 swaps the two strides.  Writes the number of
+ * wrong entries and the largest error (host outputs).  No counterpart in the paper:
+ * a check of the hardware encoding the tensor-core product relies on. */
+int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream);
 
 /* Whole-GPU issue-rate probe used for roofline denominators: kind 0 = FP32 FFMA,
  * 1 = MUFU ex2, 2 = FP64 DFMA.  Writes operations per second to *ops_per_s (host).

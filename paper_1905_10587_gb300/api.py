@@ -213,6 +213,17 @@ def peak_probe(kind: int) -> float:
     return v.value
 
 
+def tc_selftest(variant: int = 0):
+    """(mismatches, max_err) of the tcgen05 known-answer test."""
+    lib = L.load()
+    m, e = C.c_int(), C.c_float()
+    rc = lib.krr_tc_selftest(variant, C.byref(m), C.byref(e),
+                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise KRRError(rc, "tensor-core self-test failed to run")
+    return m.value, e.value
+
+
 def solve(X, y, sigma: float, beta: float, k: int, seed: int = 0, tol: float = 1e-6, **opts):
     """One-call solve through the public API.  X, y may live on the host: they are copied
     to the current CUDA device, and alpha comes back on the device of the inputs."""

@@ -176,6 +176,15 @@ static int build_from_anchors(krr_ctx* ctx, const int* S_dev, int k_eff) {
     return KRR_OK;
 }
 
+static bool use_tc(const krr_ctx* ctx, int d) { return ctx->opts.precision == 1 && kernel_dim(d) <= 16; }
+
+// (K + beta I) V for the built point set, on the path opts.precision selects.
+static int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q) {
+    if (ctx->FA)
+        return launch_kmvm_tc(ctx, ctx->FA, ctx->n, ctx->FB, ctx->n, ctx->d, (float)ctx->beta, V, nrhs, Q);
+    return launch_kmvm(ctx, ctx->P, ctx->n, ctx->P, ctx->n, ctx->d, (float)ctx->beta, V, nrhs, Q);
+}
+
 static int build_common(krr_ctx* ctx, const float* X, long long n, int d, double sigma,
                         double beta) {
     ctx->built = false;
@@ -192,6 +201,13 @@ static int build_common(krr_ctx* ctx, const float* X, long long n, int d, double
     Phase ph(ctx, PH_PREP);
     KRR_RET(launch_mean(ctx, X, n, d, mu));
     KRR_RET(launch_pack(ctx, X, n, d, mu, ctx->s, ctx->P));
+    ctx->FA = ctx->FB = nullptr;
+    if (use_tc(ctx, d)) {
+        KRR_RET(bufT(ctx, "tc_FA", tc_feature_bytes(n, d), &ctx->FA));
+        KRR_RET(bufT(ctx, "tc_FB", tc_feature_bytes(n, d), &ctx->FB));
+        KRR_RET(launch_tc_features(ctx, ctx->P, n, d, 0, ctx->FA));
+        KRR_RET(launch_tc_features(ctx, ctx->P, n, d, 1, ctx->FB));
+    }
     return KRR_OK;
 }
 
@@ -222,7 +238,8 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
     else krr_default_opts(&ctx->opts);
     if (ctx->opts.max_iter < 1 || ctx->opts.refine_max < 1 || ctx->opts.oversample < 0 ||
         ctx->opts.check_every < 1 || !(ctx->opts.inner_tol > 0.0) || ctx->opts.inner_tol >= 1.0 ||
-        ctx->opts.residual < 0 || ctx->opts.residual > 1 ||
+        ctx->opts.residual < 0 || ctx->opts.residual > 1 || ctx->opts.precision < 0 ||
+        ctx->opts.precision > 1 ||
         !(ctx->opts.anchor_rtol >= 0.0)) {
         delete ctx;
         return KRR_E_INVAL;
@@ -323,6 +340,21 @@ int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long 
     } else {
         KRR_RET(bufT(ctx, "kmvm_Pr", (size_t)nr * ps, &Pr));
         KRR_RET(launch_pack(ctx, Xr, nr, d, mu, s, Pr));
+    }
+    if (use_tc(ctx, d)) {
+        unsigned char *FA, *FB;
+        KRR_RET(bufT(ctx, "kmvm_FA", tc_feature_bytes(nr, d), &FA));
+        KRR_RET(bufT(ctx, "kmvm_FB", tc_feature_bytes(nc, d), &FB));
+        KRR_RET(launch_tc_features(ctx, Pr, nr, d, 0, FA));
+        KRR_RET(launch_tc_features(ctx, Pc, nc, d, 1, FB));
+        KRR_RET(launch_kmvm_tc(ctx, FA, nr, FB, nc, d, (float)beta, V, nrhs, Q));
+        int* err;
+        int herr = 0;
+        KRR_RET(bufT(ctx, "tc_err", 1, &err));
+        KRR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (herr) return fail(ctx, KRR_E_CUDA, "tensor-core product: a bounded wait timed out");
+        return KRR_OK;
     }
     KRR_RET(launch_kmvm(ctx, Pr, nr, Pc, nc, d, (float)beta, V, nrhs, Q));
     return KRR_OK;
@@ -578,7 +610,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         while (true) {
             {
                 Phase ph(ctx, PH_KMVM);
-                KRR_RET(launch_kmvm(ctx, ctx->P, n, ctx->P, n, ctx->d, (float)ctx->beta, p, nrhs, q));
+                KRR_RET(square_product(ctx, p, nrhs, q));
             }
             inf.mvm_count++;
             {

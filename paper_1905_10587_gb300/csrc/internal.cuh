@@ -108,6 +108,8 @@ struct krr_ctx {
     float* F = nullptr;        // n x ldF, F = K(X, X_S) L1^{-T}
     double* T2 = nullptr;      // k_eff x k_eff, L2^{-1} (lower)
     double* T2t = nullptr;     // its transpose
+    unsigned char* FA = nullptr;   // tensor-core features of X (row role), precision 1
+    unsigned char* FB = nullptr;   // tensor-core features of X (column role)
     krr::CGScalars* cg = nullptr;
     krr::CGScalars* cg_host = nullptr;   // pinned mirror
 
@@ -171,6 +173,16 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
 // R = Y - (K + beta I) A in FP64 (Y float, A/R double)
 int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);
+
+int launch_kmvm_reduce(krr_ctx* ctx, const float* part, int splits, int nr, int nrhs, const float* V,
+                       int ldv, float beta, float* Q, int ldq);
+
+// tc_kmvm.cu: BF16x3 tcgen05 product (d <= 16).  Features: role 0 rows, 1 columns.
+int tc_feature_kp(int d);
+size_t tc_feature_bytes(long long n, int d);
+int launch_tc_features(krr_ctx* ctx, const float* P, long long n, int d, int role, unsigned char* out);
+int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
+                   long long nc, int d, float beta, const float* V, int nrhs, float* Q);
 
 // residual_ff.cu: same contract in float-float on the FP32 pipe (d <= 16; else FP64)
 int launch_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,

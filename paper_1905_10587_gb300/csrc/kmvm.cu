@@ -223,6 +223,15 @@ __global__ void k_kmvm_reduce(const float* __restrict__ part, int splits, int nr
     Q[(size_t)q * ldq + i] = s;
 }
 
+int launch_kmvm_reduce(krr_ctx* ctx, const float* part, int splits, int nr, int nrhs, const float* V,
+                       int ldv, float beta, float* Q, int ldq) {
+    const long long tot = (long long)nr * nrhs;
+    k_kmvm_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, splits, nr, nrhs, V, ldv, beta, Q,
+                                                                ldq);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
 template <int D, int NRHS>
 constexpr int kmvm_rows() {
     return (D > 32) ? 1 : (D > 16 || NRHS >= 16 || (NRHS >= 8 && D >= 8)) ? 2 : 4;

@@ -1,0 +1,516 @@
+// Tensor-core (tcgen05) kernel product for sm_103a.
+//
+// The exponent of every pair is an inner product: with xh = (x - mu) sqrt(s) and
+// a = -||xh||^2, t_ij = 2 xh_i . xh_j + a_i + a_j = -s ||x_i - x_j||^2 (log2 units).
+// Each FP32 value v is split into three BF16 pieces v = h + m + l (24 significant
+// bits), and t_ij is one BF16 GEMM over an augmented K dimension:
+//     row i    : [2h, 2h, 2m, 2h, 2m, 2l]_c ... , a1, a2, a3, 1, 1, 1
+//     column j : [ H,  M,  H,  L,  M,  H]_c ... ,  1,  1,  1, A1, A2, A3
+// (the products hH + hM + mH + hL + mM + lH keep every term above 2^-24 relative).
+// A CTA owns 256 rows (two M = 128 MMAs) and streams 128-column tiles: features
+// arrive by cp.async.bulk on an mbarrier, tcgen05.mma accumulates t into TMEM
+// (two 256-column buffers, so the MMA of tile t+1 overlaps the epilogue of tile t),
+// and the epilogue reads TMEM with tcgen05.ld and does one ex2 (MUFU) and one FFMA
+// per pair and right-hand side.  Every wait is bounded; on timeout the kernel sets
+// an error word, stops issuing work, frees its TMEM and returns.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cuda_bf16.h>
+
+namespace krr {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (about 2^32 cycles, ~2 s): false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 32)) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulation.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit columns: thread = lane, r[c] = column c.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x
+// 16 bytes stored as contiguous 128-byte blocks; lbo = byte distance between core
+// matrices adjacent along K, sbo = between 8-row groups; bits 46-47 = 1 (version),
+// layout type 0 (no swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (r, k) in the core-matrix tiled layout of a tile with Kp columns.
+__host__ __device__ inline uint32_t tile_off(int r, int k, int Kp) {
+    return (uint32_t)((((r >> 3) * (Kp >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// ------------------------------------------------------------------ self-test
+// One M=128, N=32, K=16 MMA on small integers (exact in BF16 and FP32); out[r*32 + c]
+// receives D.  variant 0 uses lbo = 128 (K neighbours), sbo = 256 (row groups);
+// variant 1 swaps them.  Every address stays inside the 5 KB of operands.
+__global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restrict__ out,
+                                                     int* __restrict__ err) {
+    __shared__ __align__(1024) unsigned char sA[128 * 16 * 2];
+    __shared__ __align__(1024) unsigned char sB[32 * 16 * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < 128 * 16; e += 128) {
+        const int r = e / 16, k = e % 16;
+        const float v = (float)((r % 7) - 3 + (k % 3));
+        *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(r, k, 16)) = __float2bfloat16_rn(v);
+    }
+    for (int e = tid; e < 32 * 16; e += 128) {
+        const int c = e / 16, k = e % 16;
+        const float v = (float)((c % 5) - 2 + (k % 4));
+        *reinterpret_cast<__nv_bfloat16*>(sB + tile_off(c, k, 16)) = __float2bfloat16_rn(v);
+    }
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (warp == 0) tmem_alloc(&tbase, 32);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tbase;
+    const uint32_t lbo = variant == 0 ? 128u : 256u, sbo = variant == 0 ? 256u : 128u;
+    if (tid == 0) {
+        mma_bf16(tmem, smem_desc(smem_u32(sA), lbo, sbo), smem_desc(smem_u32(sB), lbo, sbo),
+                 idesc_bf16(128, 32), 0u);
+        mma_commit(&bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait(&bar, 0)) != 0;
+    if (!ok && tid == 0) atomicExch(err, 1);
+    tc_fence_after();
+    if (ok) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
+        tmem_wait_ld();
+        const int row = warp * 32 + lane;
+        for (int c = 0; c < 32; ++c) out[row * 32 + c] = __uint_as_float(r[c]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 32);
+}
+
+// ------------------------------------------------------------------ features
+// bf16 pieces of a float: v = h + m + l
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+// Features of point i (packed xh, a at P[i*ps + dk]) written into the tiled layout:
+// role 0 = row operand, role 1 = column operand.  Rows beyond n are zero.
+__global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, int ps, int Kp,
+                              int role, long long nrows_pad, unsigned char* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows_pad) return;
+    const long long tile = i >> 7;
+    const int r = (int)(i & 127);
+    unsigned char* base = out + tile * (128LL * Kp * 2);
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+    auto put = [&](int k, __nv_bfloat16 v) {
+        *reinterpret_cast<__nv_bfloat16*>(base + tile_off(r, k, Kp)) = v;
+    };
+    if (i >= n) {
+        for (int k = 0; k < Kp; ++k) put(k, zero);
+        return;
+    }
+    int k = 0;
+    for (int c = 0; c < dk; ++c) {
+        const float x = P[i * ps + c];
+        __nv_bfloat16 h, m, l;
+        if (role == 0) {
+            split3(2.f * x, h, m, l);
+            put(k++, h); put(k++, h); put(k++, m); put(k++, h); put(k++, m); put(k++, l);
+        } else {
+            split3(x, h, m, l);
+            put(k++, h); put(k++, m); put(k++, h); put(k++, l); put(k++, m); put(k++, h);
+        }
+    }
+    __nv_bfloat16 a1, a2, a3;
+    split3(P[i * ps + dk], a1, a2, a3);
+    if (role == 0) {
+        put(k++, a1); put(k++, a2); put(k++, a3); put(k++, one); put(k++, one); put(k++, one);
+    } else {
+        put(k++, one); put(k++, one); put(k++, one); put(k++, a1); put(k++, a2); put(k++, a3);
+    }
+    for (; k < Kp; ++k) put(k, zero);
+}
+
+// ------------------------------------------------------------------ product kernel
+constexpr int TC_THREADS = 256;   // 8 warps: (half, quarter) of the 256-row block
+constexpr int TC_BN = 128;        // columns per tile
+constexpr int TC_ROWS = 256;      // rows per work item
+
+struct TcShared {
+    uint64_t bar_a, bar_ld[2], bar_mma[2];
+    uint32_t tbase;
+    int abort;
+};
+
+template <int NRHS>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
+          int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
+          int tiles_per_split, float beta, const float* __restrict__ Vbeta, int ldvb,
+          float* __restrict__ Q, float* __restrict__ part, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t tileA = 128u * Kp * 2u;            // bytes of one 128-row feature tile
+    unsigned char* sA = smem;                         // 2 tiles (256 rows)
+    unsigned char* sB0 = smem + 2 * tileA;            // stage 0
+    unsigned char* sB1 = sB0 + tileA;                 // stage 1
+    float* sV0 = reinterpret_cast<float*>(sB1 + tileA);
+    float* sV1 = sV0 + NRHS * TC_BN;
+    TcShared* sh = reinterpret_cast<TcShared*>(sV1 + NRHS * TC_BN);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int half = warp >> 2, quarter = warp & 3;
+    if (tid == 0) {
+        mbar_init(&sh->bar_a, 1);
+        mbar_init(&sh->bar_ld[0], 1);
+        mbar_init(&sh->bar_ld[1], 1);
+        mbar_init(&sh->bar_mma[0], 1);
+        mbar_init(&sh->bar_mma[1], 1);
+        sh->abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) tmem_alloc(&sh->tbase, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tbase;
+    const uint32_t idesc = idesc_bf16(128, TC_BN);
+    const uint32_t sbo = (uint32_t)Kp * 16u;          // (Kp / 8) core matrices x 128 bytes
+    const int ntiles = (nc + TC_BN - 1) / TC_BN;
+    const uint32_t vbytes = NRHS * TC_BN * 4u;
+    uint32_t ph_a = 0, ph_ld0 = 0, ph_ld1 = 0, ph_m0 = 0, ph_m1 = 0;
+    bool ok = true;
+
+    auto issue_load = [&](int t, int stage) {   // tid 0 only
+        uint64_t* bar = &sh->bar_ld[stage];
+        unsigned char* dB = stage ? sB1 : sB0;
+        float* dV = stage ? sV1 : sV0;
+        mbar_expect_tx(bar, tileA + vbytes);
+        bulk_g2s(dB, FB + (size_t)t * tileA, tileA, bar);
+        for (int q = 0; q < NRHS; ++q)
+            bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u, bar);
+    };
+    auto issue_mma = [&](int stage) {   // tid 0 only
+        const uint32_t b_addr = smem_u32(stage ? sB1 : sB0);
+        const uint32_t a_addr = smem_u32(sA);
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t d = tmem + (uint32_t)(stage * 256 + h * 128);
+            for (int kk = 0; kk < Kp / 16; ++kk) {
+                const uint64_t ad = smem_desc(a_addr + h * tileA + kk * 256u, 128u, sbo);
+                const uint64_t bd = smem_desc(b_addr + kk * 256u, 128u, sbo);
+                mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            }
+        }
+        mma_commit(&sh->bar_mma[stage]);
+    };
+
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const int rb = item / splits, sp = item - rb * splits;
+        const int t0 = sp * tiles_per_split;
+        const int t1 = min(t0 + tiles_per_split, ntiles);
+        const int nt = t1 - t0;
+        float acc[NRHS];
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) acc[q] = 0.f;
+        if (nt > 0) {
+            if (tid == 0) {
+                mbar_expect_tx(&sh->bar_a, 2 * tileA);
+                bulk_g2s(sA, FA + (size_t)rb * 2 * tileA, 2 * tileA, &sh->bar_a);
+                issue_load(t0, 0);
+                if (nt > 1) issue_load(t0 + 1, 1);
+            }
+            ok = __syncthreads_and(mbar_wait(&sh->bar_a, ph_a)) != 0;
+            ph_a ^= 1;
+            for (int t = 0; t < nt && ok; ++t) {
+                const int s = t & 1;
+                if (t == 0) {
+                    ok = __syncthreads_and(mbar_wait(&sh->bar_ld[0], ph_ld0)) != 0;
+                    ph_ld0 ^= 1;
+                    if (ok && tid == 0) {
+                        tc_fence_after();
+                        issue_mma(0);
+                    }
+                }
+                if (ok && t + 1 < nt) {
+                    const int s1 = (t + 1) & 1;
+                    ok = __syncthreads_and(mbar_wait(&sh->bar_ld[s1], s1 ? ph_ld1 : ph_ld0)) != 0;
+                    if (s1) ph_ld1 ^= 1; else ph_ld0 ^= 1;
+                    if (ok && tid == 0) {
+                        tc_fence_after();
+                        issue_mma(s1);
+                    }
+                }
+                if (!ok) break;
+                ok = __syncthreads_and(mbar_wait(&sh->bar_mma[s], s ? ph_m1 : ph_m0)) != 0;
+                if (s) ph_m1 ^= 1; else ph_m0 ^= 1;
+                if (!ok) break;
+                tc_fence_after();
+                const float* v = s ? sV1 : sV0;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * 256 + half * 128);
+#pragma unroll 1
+                for (int c = 0; c < TC_BN / 32; ++c) {
+                    uint32_t r[32];
+                    tmem_ld32(tb + c * 32, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        float e[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) e[u] = ex2f(__uint_as_float(r[4 * j4 + u]));
+#pragma unroll
+                        for (int q = 0; q < NRHS; ++q) {
+                            const float4 vv = *reinterpret_cast<const float4*>(v + q * TC_BN + c * 32 + 4 * j4);
+                            acc[q] = fmaf(e[0], vv.x, fmaf(e[1], vv.y, fmaf(e[2], vv.z, fmaf(e[3], vv.w, acc[q]))));
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0 && t + 2 < nt) issue_load(t0 + t + 2, s);
+            }
+        }
+        if (!ok) break;   // uniform: every decision above went through __syncthreads_and
+        const long long row = (long long)rb * TC_ROWS + half * 128 + quarter * 32 + lane;
+        if (row < nr) {
+            if (part == nullptr) {
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q)
+                    Q[(size_t)q * nr + row] = acc[q] + (beta != 0.f ? beta * Vbeta[(size_t)q * ldvb + row] : 0.f);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) part[((size_t)sp * NRHS + q) * nr + row] = acc[q];
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        sh->abort = 1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (sh->abort) {
+        // let in-flight MMAs drain (bounded) before the TMEM is released
+        mbar_wait(&sh->bar_mma[0], ph_m0);
+        mbar_wait(&sh->bar_mma[1], ph_m1);
+    }
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------------ host side
+int tc_feature_kp(int d) { return ((6 * kernel_dim(d) + 6) + 15) / 16 * 16; }
+
+int launch_tc_features(krr_ctx* ctx, const float* P, long long n, int d, int role,
+                       unsigned char* out) {
+    const int dk = kernel_dim(d), Kp = tc_feature_kp(d);
+    const long long npad = (n + 255) / 256 * 256;
+    k_tc_features<<<ceil_div(npad, 256), 256, 0, ctx->stream>>>(P, n, dk, packed_stride(d), Kp, role,
+                                                                npad, out);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+size_t tc_feature_bytes(long long n, int d) {
+    return (size_t)((n + 255) / 256 * 256) * tc_feature_kp(d) * 2;
+}
+
+typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
+                      int, int, int, float, const float*, int, float*, float*, int*);
+
+int choose_splits_public(int nblk, int ntiles, int slots);
+
+// Q = K(rows, cols) V + beta V using features FA (rows) and FB (cols).
+int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
+                   long long nc, int d, float beta, const float* V, int nrhs, float* Q) {
+    if (kernel_dim(d) > 16) return fail(ctx, KRR_E_INVAL, "tensor-core product needs d <= 16");
+    const int Kp = tc_feature_kp(d);
+    const int ncp = (int)((nc + TC_BN - 1) / TC_BN * TC_BN);
+    int* err;
+    KRR_RET(bufT(ctx, "tc_err", 1, &err));
+    KRR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    int done = 0;
+    while (done < nrhs) {
+        const int left = nrhs - done;
+        const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        tc_fn fn = chunk == 1 ? &k_kmvm_tc<1> : chunk == 2 ? &k_kmvm_tc<2> : chunk == 4 ? &k_kmvm_tc<4>
+                 : chunk == 8 ? &k_kmvm_tc<8> : &k_kmvm_tc<16>;
+        // V padded to whole 128-column tiles, RHS-major (16-byte aligned bulk copies)
+        float* Vp;
+        KRR_RET(bufT(ctx, "tc_vpad", (size_t)chunk * ncp, &Vp));
+        KRR_TRY_CUDA(cudaMemsetAsync(Vp, 0, sizeof(float) * chunk * ncp, ctx->stream));
+        KRR_TRY_CUDA(cudaMemcpy2DAsync(Vp, sizeof(float) * ncp, V + (size_t)done * nc, sizeof(float) * nc,
+                                       sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
+        const uint32_t tileA = 128u * Kp * 2u;
+        const size_t smem = 4 * (size_t)tileA + 2 * (size_t)chunk * TC_BN * 4 + 128;
+        const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
+        KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_launch));
+        const int nrb = (int)ceil_div(nr, TC_ROWS);
+        const int ntiles = ncp / TC_BN;
+        int splits = choose_splits_public(nrb, ntiles, ctx->num_sms);
+        const int tps = (ntiles + splits - 1) / splits;
+        splits = (ntiles + tps - 1) / tps;
+        const int items = nrb * splits;
+        float* part = nullptr;
+        if (splits > 1) KRR_RET(bufT(ctx, "tc_part", (size_t)splits * chunk * nr, &part));
+        const int grid = std::min(items, ctx->num_sms);
+        fn<<<grid, TC_THREADS, smem_launch, ctx->stream>>>(FA, FB, Kp, (int)nr, (int)nc, ncp, Vp, items,
+                                                           splits, tps, beta, V + (size_t)done * nc,
+                                                           (int)nc, Q + (size_t)done * nr, part, err);
+        KRR_CHECK_LAUNCH();
+        if (splits > 1) {
+            KRR_RET(launch_kmvm_reduce(ctx, part, splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
+                                       beta, Q + (size_t)done * nr, (int)nr));
+        }
+        done += chunk;
+    }
+    return KRR_OK;
+}
+
+}  // namespace krr
+
+using namespace krr;
+
+// Known-answer test of the tcgen05 descriptor encodings (host entry, see krr.h).
+extern "C" int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream_v) {
+    if (!mismatches || !max_err || variant < 0 || variant > 1) return KRR_E_INVAL;
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    float* out = nullptr;
+    int* err = nullptr;
+    if (cudaMalloc(&out, 128 * 32 * sizeof(float)) != cudaSuccess) return KRR_E_NOMEM;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaFree(out);
+        return KRR_E_NOMEM;
+    }
+    cudaMemsetAsync(err, 0, sizeof(int), stream);
+    cudaMemsetAsync(out, 0, 128 * 32 * sizeof(float), stream);
+    k_tc_selftest<<<1, 128, 0, stream>>>(variant, out, err);
+    float h[128 * 32];
+    int herr = 0;
+    cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    const cudaError_t e = cudaStreamSynchronize(stream);
+    cudaFree(out);
+    cudaFree(err);
+    if (e != cudaSuccess) return KRR_E_CUDA;
+    if (herr) return KRR_E_CUDA;
+    int bad = 0;
+    float mx = 0.f;
+    for (int r = 0; r < 128; ++r)
+        for (int c = 0; c < 32; ++c) {
+            float ref = 0.f;
+            for (int k = 0; k < 16; ++k)
+                ref += (float)((r % 7) - 3 + (k % 3)) * (float)((c % 5) - 2 + (k % 4));
+            const float d = std::fabs(h[r * 32 + c] - ref);
+            mx = std::max(mx, d);
+            if (d > 0.f) ++bad;
+        }
+    *mismatches = bad;
+    *max_err = mx;
+    return KRR_OK;
+}
