@@ -236,12 +236,13 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
 }
 
 // ------------------------------------------------------------------ product kernel
-constexpr int TC_THREADS = 256;   // 8 warps: (half, quarter) of the 256-row block
+constexpr int TC_THREADS = 512;   // 16 warps: (column group, half, lane quarter)
 constexpr int TC_BN = 128;        // columns per tile
 constexpr int TC_ROWS = 256;      // rows per work item
+constexpr int TC_NS = 4;          // pipeline stages for column tiles
 
 struct TcShared {
-    uint64_t bar_a, bar_ld[2], bar_mma[2];
+    uint64_t bar_a, bar_ld[TC_NS], bar_mma[2];
     uint32_t tbase;
     int abort;
 };
@@ -255,18 +256,17 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t tileA = 128u * Kp * 2u;            // bytes of one 128-row feature tile
     unsigned char* sA = smem;                         // 2 tiles (256 rows)
-    unsigned char* sB0 = smem + 2 * tileA;            // stage 0
-    unsigned char* sB1 = sB0 + tileA;                 // stage 1
-    float* sV0 = reinterpret_cast<float*>(sB1 + tileA);
-    float* sV1 = sV0 + NRHS * TC_BN;
-    TcShared* sh = reinterpret_cast<TcShared*>(sV1 + NRHS * TC_BN);
+    unsigned char* sB = smem + 2 * tileA;             // TC_NS column tiles
+    float* sV = reinterpret_cast<float*>(sB + TC_NS * tileA);   // TC_NS x NRHS x TC_BN
+    float* sRed = sV + TC_NS * NRHS * TC_BN;                    // 256 x NRHS partial sums
+    TcShared* sh = reinterpret_cast<TcShared*>(sRed + TC_ROWS * NRHS);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int half = warp >> 2, quarter = warp & 3;
+    const int quarter = warp & 3, half = (warp >> 2) & 1, cgrp = warp >> 3;
+    const int lrow = half * 128 + quarter * 32 + lane;   // row inside the 256-row block
     if (tid == 0) {
         mbar_init(&sh->bar_a, 1);
-        mbar_init(&sh->bar_ld[0], 1);
-        mbar_init(&sh->bar_ld[1], 1);
+        for (int s = 0; s < TC_NS; ++s) mbar_init(&sh->bar_ld[s], 1);
         mbar_init(&sh->bar_mma[0], 1);
         mbar_init(&sh->bar_mma[1], 1);
         sh->abort = 0;
@@ -282,30 +282,34 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     const uint32_t sbo = (uint32_t)Kp * 16u;          // (Kp / 8) core matrices x 128 bytes
     const int ntiles = (nc + TC_BN - 1) / TC_BN;
     const uint32_t vbytes = NRHS * TC_BN * 4u;
-    uint32_t ph_a = 0, ph_ld0 = 0, ph_ld1 = 0, ph_m0 = 0, ph_m1 = 0;
+    uint32_t ph_a = 0, ph_ld = 0, ph_m = 0;           // parity bits per barrier
     bool ok = true;
 
     auto issue_load = [&](int t, int stage) {   // tid 0 only
         uint64_t* bar = &sh->bar_ld[stage];
-        unsigned char* dB = stage ? sB1 : sB0;
-        float* dV = stage ? sV1 : sV0;
         mbar_expect_tx(bar, tileA + vbytes);
-        bulk_g2s(dB, FB + (size_t)t * tileA, tileA, bar);
+        bulk_g2s(sB + stage * tileA, FB + (size_t)t * tileA, tileA, bar);
+        float* dV = sV + stage * NRHS * TC_BN;
         for (int q = 0; q < NRHS; ++q)
             bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u, bar);
     };
-    auto issue_mma = [&](int stage) {   // tid 0 only
-        const uint32_t b_addr = smem_u32(stage ? sB1 : sB0);
+    auto issue_mma = [&](int stage, int buf) {   // tid 0 only
+        const uint32_t b_addr = smem_u32(sB + stage * tileA);
         const uint32_t a_addr = smem_u32(sA);
         for (int h = 0; h < 2; ++h) {
-            const uint32_t d = tmem + (uint32_t)(stage * 256 + h * 128);
+            const uint32_t d = tmem + (uint32_t)(buf * 256 + h * 128);
             for (int kk = 0; kk < Kp / 16; ++kk) {
                 const uint64_t ad = smem_desc(a_addr + h * tileA + kk * 256u, 128u, sbo);
                 const uint64_t bd = smem_desc(b_addr + kk * 256u, 128u, sbo);
                 mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
             }
         }
-        mma_commit(&sh->bar_mma[stage]);
+        mma_commit(&sh->bar_mma[buf]);
+    };
+    auto wait_ld = [&](int stage) {
+        const bool r = __syncthreads_and(mbar_wait(&sh->bar_ld[stage], (ph_ld >> stage) & 1u)) != 0;
+        ph_ld ^= 1u << stage;
+        return r;
     };
 
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
@@ -313,76 +317,95 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         const int t0 = sp * tiles_per_split;
         const int t1 = min(t0 + tiles_per_split, ntiles);
         const int nt = t1 - t0;
-        float acc[NRHS];
+        constexpr int NA = NRHS >= 8 ? 1 : 4;   // independent FMA chains per right-hand side
+        float acc[NRHS][NA];
 #pragma unroll
-        for (int q = 0; q < NRHS; ++q) acc[q] = 0.f;
+        for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+            for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
         if (nt > 0) {
             if (tid == 0) {
                 mbar_expect_tx(&sh->bar_a, 2 * tileA);
                 bulk_g2s(sA, FA + (size_t)rb * 2 * tileA, 2 * tileA, &sh->bar_a);
-                issue_load(t0, 0);
-                if (nt > 1) issue_load(t0 + 1, 1);
+                for (int i = 0; i < TC_NS && i < nt; ++i) issue_load(t0 + i, i);
             }
             ok = __syncthreads_and(mbar_wait(&sh->bar_a, ph_a)) != 0;
-            ph_a ^= 1;
+            ph_a ^= 1u;
             for (int t = 0; t < nt && ok; ++t) {
-                const int s = t & 1;
+                const int buf = t & 1;
                 if (t == 0) {
-                    ok = __syncthreads_and(mbar_wait(&sh->bar_ld[0], ph_ld0)) != 0;
-                    ph_ld0 ^= 1;
+                    ok = wait_ld(0);
                     if (ok && tid == 0) {
                         tc_fence_after();
-                        issue_mma(0);
+                        issue_mma(0, 0);
                     }
                 }
                 if (ok && t + 1 < nt) {
-                    const int s1 = (t + 1) & 1;
-                    ok = __syncthreads_and(mbar_wait(&sh->bar_ld[s1], s1 ? ph_ld1 : ph_ld0)) != 0;
-                    if (s1) ph_ld1 ^= 1; else ph_ld0 ^= 1;
+                    ok = wait_ld((t + 1) % TC_NS);
                     if (ok && tid == 0) {
                         tc_fence_after();
-                        issue_mma(s1);
+                        issue_mma((t + 1) % TC_NS, (t + 1) & 1);
                     }
                 }
                 if (!ok) break;
-                ok = __syncthreads_and(mbar_wait(&sh->bar_mma[s], s ? ph_m1 : ph_m0)) != 0;
-                if (s) ph_m1 ^= 1; else ph_m0 ^= 1;
+                ok = __syncthreads_and(mbar_wait(&sh->bar_mma[buf], (ph_m >> buf) & 1u)) != 0;
+                ph_m ^= 1u << buf;
                 if (!ok) break;
                 tc_fence_after();
-                const float* v = s ? sV1 : sV0;
-                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * 256 + half * 128);
-#pragma unroll 1
-                for (int c = 0; c < TC_BN / 32; ++c) {
-                    uint32_t r[32];
-                    tmem_ld32(tb + c * 32, r);
-                    tmem_wait_ld();
+                const float* v = sV + (t % TC_NS) * NRHS * TC_BN + cgrp * 64;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) +
+                                    (uint32_t)(buf * 256 + half * 128 + cgrp * 64);
+                uint32_t r0[32], r1[32];
+                tmem_ld32(tb, r0);
+                tmem_ld32(tb + 32, r1);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int j4 = 0; j4 < 8; ++j4) {
-                        float e[4];
+                for (int j4 = 0; j4 < 16; ++j4) {
+                    float e[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) e[u] = ex2f(__uint_as_float(r[4 * j4 + u]));
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 4 * j4 + u;
+                        e[u] = ex2f(__uint_as_float(c < 32 ? r0[c] : r1[c - 32]));
+                    }
 #pragma unroll
-                        for (int q = 0; q < NRHS; ++q) {
-                            const float4 vv = *reinterpret_cast<const float4*>(v + q * TC_BN + c * 32 + 4 * j4);
-                            acc[q] = fmaf(e[0], vv.x, fmaf(e[1], vv.y, fmaf(e[2], vv.z, fmaf(e[3], vv.w, acc[q]))));
-                        }
+                    for (int q = 0; q < NRHS; ++q) {
+                        const float4 vv = *reinterpret_cast<const float4*>(v + q * TC_BN + 4 * j4);
+                        acc[q][0 % NA] = fmaf(e[0], vv.x, acc[q][0 % NA]);
+                        acc[q][1 % NA] = fmaf(e[1], vv.y, acc[q][1 % NA]);
+                        acc[q][2 % NA] = fmaf(e[2], vv.z, acc[q][2 % NA]);
+                        acc[q][3 % NA] = fmaf(e[3], vv.w, acc[q][3 % NA]);
                     }
                 }
                 tc_fence_before();
                 __syncthreads();
-                if (tid == 0 && t + 2 < nt) issue_load(t0 + t + 2, s);
+                if (tid == 0 && t + TC_NS < nt) issue_load(t0 + t + TC_NS, t % TC_NS);
             }
         }
         if (!ok) break;   // uniform: every decision above went through __syncthreads_and
-        const long long row = (long long)rb * TC_ROWS + half * 128 + quarter * 32 + lane;
-        if (row < nr) {
-            if (part == nullptr) {
+        // combine the two column groups of each row
+        float tot[NRHS];
 #pragma unroll
-                for (int q = 0; q < NRHS; ++q)
-                    Q[(size_t)q * nr + row] = acc[q] + (beta != 0.f ? beta * Vbeta[(size_t)q * ldvb + row] : 0.f);
-            } else {
+        for (int q = 0; q < NRHS; ++q) {
+            tot[q] = acc[q][0];
 #pragma unroll
-                for (int q = 0; q < NRHS; ++q) part[((size_t)sp * NRHS + q) * nr + row] = acc[q];
+            for (int a = 1; a < NA; ++a) tot[q] += acc[q][a];
+        }
+        if (cgrp == 1) {
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) sRed[q * TC_ROWS + lrow] = tot[q];
+        }
+        __syncthreads();
+        if (cgrp == 0) {
+            const long long row = (long long)rb * TC_ROWS + lrow;
+            if (row < nr) {
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) {
+                    const float sum = tot[q] + sRed[q * TC_ROWS + lrow];
+                    if (part == nullptr)
+                        Q[(size_t)q * nr + row] = sum + (beta != 0.f ? beta * Vbeta[(size_t)q * ldvb + row] : 0.f);
+                    else
+                        part[((size_t)sp * NRHS + q) * nr + row] = sum;
+                }
             }
         }
         __syncthreads();
@@ -395,8 +418,8 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     __syncthreads();
     if (sh->abort) {
         // let in-flight MMAs drain (bounded) before the TMEM is released
-        mbar_wait(&sh->bar_mma[0], ph_m0);
-        mbar_wait(&sh->bar_mma[1], ph_m1);
+        mbar_wait(&sh->bar_mma[0], ph_m & 1u);
+        mbar_wait(&sh->bar_mma[1], (ph_m >> 1) & 1u);
     }
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 512);
@@ -446,7 +469,8 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         KRR_TRY_CUDA(cudaMemcpy2DAsync(Vp, sizeof(float) * ncp, V + (size_t)done * nc, sizeof(float) * nc,
                                        sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
         const uint32_t tileA = 128u * Kp * 2u;
-        const size_t smem = 4 * (size_t)tileA + 2 * (size_t)chunk * TC_BN * 4 + 128;
+        const size_t smem = (2 + TC_NS) * (size_t)tileA + (size_t)TC_NS * chunk * TC_BN * 4 +
+                            (size_t)TC_ROWS * chunk * 4 + 256;
         const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
         KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem_launch));
