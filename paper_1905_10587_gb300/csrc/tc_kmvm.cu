@@ -236,39 +236,53 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
 }
 
 // ------------------------------------------------------------------ product kernel
-constexpr int TC_THREADS = 512;   // 16 warps: (column group, half, lane quarter)
+// Warp-specialised persistent CTA (one per SM): warp 0 lane 0 streams feature tiles
+// with cp.async.bulk, warp 1 lane 0 issues tcgen05.mma, warps 2..17 are the epilogue.
+// Hand-offs are mbarrier full/empty pairs only (no block-wide barrier in the loop):
+//   a_full / a_empty          the 256-row operand of the current work item
+//   s_full[s] / s_empty[s]    column tile stage s (empty needs the MMA commit and all
+//                             16 epilogue warps, because the epilogue reads V from it)
+//   t_full[b] / t_empty[b]    TMEM accumulator buffer b (2 x 256 columns)
+constexpr int TC_EPI_WARPS = 16;
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_BN = 128;        // columns per tile
 constexpr int TC_ROWS = 256;      // rows per work item
 constexpr int TC_NS = 4;          // pipeline stages for column tiles
 
 struct TcShared {
-    uint64_t bar_a, bar_ld[TC_NS], bar_mma[2];
+    uint64_t a_full, a_empty, s_full[TC_NS], s_empty[TC_NS], t_full[2], t_empty[2];
     uint32_t tbase;
     int abort;
 };
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <int NRHS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
           int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
-          int tiles_per_split, float beta, const float* __restrict__ Vbeta, int ldvb,
-          float* __restrict__ Q, float* __restrict__ part, int* __restrict__ err) {
+          int tiles_per_split, float* __restrict__ part, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t tileA = 128u * Kp * 2u;            // bytes of one 128-row feature tile
     unsigned char* sA = smem;                         // 2 tiles (256 rows)
     unsigned char* sB = smem + 2 * tileA;             // TC_NS column tiles
     float* sV = reinterpret_cast<float*>(sB + TC_NS * tileA);   // TC_NS x NRHS x TC_BN
-    float* sRed = sV + TC_NS * NRHS * TC_BN;                    // 256 x NRHS partial sums
-    TcShared* sh = reinterpret_cast<TcShared*>(sRed + TC_ROWS * NRHS);
+    TcShared* sh = reinterpret_cast<TcShared*>(sV + TC_NS * NRHS * TC_BN);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quarter = warp & 3, half = (warp >> 2) & 1, cgrp = warp >> 3;
-    const int lrow = half * 128 + quarter * 32 + lane;   // row inside the 256-row block
     if (tid == 0) {
-        mbar_init(&sh->bar_a, 1);
-        for (int s = 0; s < TC_NS; ++s) mbar_init(&sh->bar_ld[s], 1);
-        mbar_init(&sh->bar_mma[0], 1);
-        mbar_init(&sh->bar_mma[1], 1);
+        mbar_init(&sh->a_full, 1);
+        mbar_init(&sh->a_empty, 1);
+        for (int s = 0; s < TC_NS; ++s) {
+            mbar_init(&sh->s_full[s], 1);
+            mbar_init(&sh->s_empty[s], 1 + TC_EPI_WARPS);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->t_full[b], 1);
+            mbar_init(&sh->t_empty[b], TC_EPI_WARPS);
+        }
         sh->abort = 0;
         fence_mbar_init();
     }
@@ -278,150 +292,145 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sh->tbase;
-    const uint32_t idesc = idesc_bf16(128, TC_BN);
-    const uint32_t sbo = (uint32_t)Kp * 16u;          // (Kp / 8) core matrices x 128 bytes
     const int ntiles = (nc + TC_BN - 1) / TC_BN;
     const uint32_t vbytes = NRHS * TC_BN * 4u;
-    uint32_t ph_a = 0, ph_ld = 0, ph_m = 0;           // parity bits per barrier
-    bool ok = true;
-
-    auto issue_load = [&](int t, int stage) {   // tid 0 only
-        uint64_t* bar = &sh->bar_ld[stage];
-        mbar_expect_tx(bar, tileA + vbytes);
-        bulk_g2s(sB + stage * tileA, FB + (size_t)t * tileA, tileA, bar);
-        float* dV = sV + stage * NRHS * TC_BN;
-        for (int q = 0; q < NRHS; ++q)
-            bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u, bar);
+    volatile int* abort = &sh->abort;
+    auto give_up = [&]() {
+        *abort = 1;
+        atomicExch(err, 1);
     };
-    auto issue_mma = [&](int stage, int buf) {   // tid 0 only
-        const uint32_t b_addr = smem_u32(sB + stage * tileA);
-        const uint32_t a_addr = smem_u32(sA);
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t d = tmem + (uint32_t)(buf * 256 + h * 128);
-            for (int kk = 0; kk < Kp / 16; ++kk) {
-                const uint64_t ad = smem_desc(a_addr + h * tileA + kk * 256u, 128u, sbo);
-                const uint64_t bd = smem_desc(b_addr + kk * 256u, 128u, sbo);
-                mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t g = 0, ic = 0;
+            for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
+                const int rb = item / splits, sp = item - rb * splits;
+                const int t0 = sp * tiles_per_split;
+                const int t1 = min(t0 + tiles_per_split, ntiles);
+                if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u)) { give_up(); break; }
+                mbar_expect_tx(&sh->a_full, 2 * tileA);
+                bulk_g2s(sA, FA + (size_t)rb * 2 * tileA, 2 * tileA, &sh->a_full);
+                for (int t = t0; t < t1; ++t, ++g) {
+                    const int s = g % TC_NS;
+                    if (!mbar_wait(&sh->s_empty[s], ((g / TC_NS) & 1u) ^ 1u)) { give_up(); break; }
+                    mbar_expect_tx(&sh->s_full[s], tileA + vbytes);
+                    bulk_g2s(sB + s * tileA, FB + (size_t)t * tileA, tileA, &sh->s_full[s]);
+                    float* dV = sV + s * NRHS * TC_BN;
+                    for (int q = 0; q < NRHS; ++q)
+                        bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u,
+                                 &sh->s_full[s]);
+                }
             }
         }
-        mma_commit(&sh->bar_mma[buf]);
-    };
-    auto wait_ld = [&](int stage) {
-        const bool r = __syncthreads_and(mbar_wait(&sh->bar_ld[stage], (ph_ld >> stage) & 1u)) != 0;
-        ph_ld ^= 1u << stage;
-        return r;
-    };
-
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-        const int rb = item / splits, sp = item - rb * splits;
-        const int t0 = sp * tiles_per_split;
-        const int t1 = min(t0 + tiles_per_split, ntiles);
-        const int nt = t1 - t0;
-        constexpr int NA = NRHS >= 8 ? 1 : 4;   // independent FMA chains per right-hand side
-        float acc[NRHS][NA];
-#pragma unroll
-        for (int q = 0; q < NRHS; ++q)
-#pragma unroll
-            for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
-        if (nt > 0) {
-            if (tid == 0) {
-                mbar_expect_tx(&sh->bar_a, 2 * tileA);
-                bulk_g2s(sA, FA + (size_t)rb * 2 * tileA, 2 * tileA, &sh->bar_a);
-                for (int i = 0; i < TC_NS && i < nt; ++i) issue_load(t0 + i, i);
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, TC_BN);
+            const uint32_t sbo = (uint32_t)Kp * 16u;   // (Kp / 8) core matrices x 128 bytes
+            const uint32_t a_addr = smem_u32(sA);
+            uint32_t g = 0, ic = 0;
+            for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
+                const int sp = item % splits;
+                const int t0 = sp * tiles_per_split;
+                const int t1 = min(t0 + tiles_per_split, ntiles);
+                if (!mbar_wait(&sh->a_full, ic & 1u)) { give_up(); break; }
+                for (int t = t0; t < t1; ++t, ++g) {
+                    const int s = g % TC_NS, b = g & 1;
+                    if (!mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u)) { give_up(); break; }
+                    if (!mbar_wait(&sh->t_empty[b], ((g >> 1) & 1u) ^ 1u)) { give_up(); break; }
+                    tc_fence_after();
+                    const uint32_t b_addr = smem_u32(sB + s * tileA);
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t d = tmem + (uint32_t)(b * 256 + h * 128);
+                        for (int kk = 0; kk < Kp / 16; ++kk) {
+                            const uint64_t ad = smem_desc(a_addr + h * tileA + kk * 256u, 128u, sbo);
+                            const uint64_t bd = smem_desc(b_addr + kk * 256u, 128u, sbo);
+                            mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(&sh->t_full[b]);
+                    mma_commit(&sh->s_empty[s]);
+                    if (t == t1 - 1) mma_commit(&sh->a_empty);
+                }
             }
-            ok = __syncthreads_and(mbar_wait(&sh->bar_a, ph_a)) != 0;
-            ph_a ^= 1u;
-            for (int t = 0; t < nt && ok; ++t) {
-                const int buf = t & 1;
-                if (t == 0) {
-                    ok = wait_ld(0);
-                    if (ok && tid == 0) {
-                        tc_fence_after();
-                        issue_mma(0, 0);
-                    }
-                }
-                if (ok && t + 1 < nt) {
-                    ok = wait_ld((t + 1) % TC_NS);
-                    if (ok && tid == 0) {
-                        tc_fence_after();
-                        issue_mma((t + 1) % TC_NS, (t + 1) & 1);
-                    }
-                }
-                if (!ok) break;
-                ok = __syncthreads_and(mbar_wait(&sh->bar_mma[buf], (ph_m >> buf) & 1u)) != 0;
-                ph_m ^= 1u << buf;
-                if (!ok) break;
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int e = warp - 2;                       // 0..15
+        const int quarter = warp & 3;                 // TMEM lanes this warp may read
+        const int half = (e >> 2) & 1, cgrp = e >> 3;
+        const int lrow = half * 128 + quarter * 32 + lane;
+        uint32_t g = 0;
+        for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
+            const int rb = item / splits, sp = item - rb * splits;
+            const int t0 = sp * tiles_per_split;
+            const int t1 = min(t0 + tiles_per_split, ntiles);
+            constexpr int NA = NRHS >= 8 ? 1 : 4;    // independent FMA chains per right-hand side
+            float acc[NRHS][NA];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+#pragma unroll
+                for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
+            bool ok = true;
+            for (int t = t0; t < t1; ++t, ++g) {
+                const int s = g % TC_NS, b = g & 1;
+                ok = mbar_wait(&sh->t_full[b], (g >> 1) & 1u) && mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) { if (lane == 0) give_up(); break; }
                 tc_fence_after();
-                const float* v = sV + (t % TC_NS) * NRHS * TC_BN + cgrp * 64;
+                const float* v = sV + s * NRHS * TC_BN + cgrp * 64;
                 const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                    (uint32_t)(buf * 256 + half * 128 + cgrp * 64);
+                                    (uint32_t)(b * 256 + half * 128 + cgrp * 64);
                 uint32_t r0[32], r1[32];
                 tmem_ld32(tb, r0);
                 tmem_ld32(tb + 32, r1);
                 tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
 #pragma unroll
                 for (int j4 = 0; j4 < 16; ++j4) {
-                    float e[4];
+                    float ev[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int c = 4 * j4 + u;
-                        e[u] = ex2f(__uint_as_float(c < 32 ? r0[c] : r1[c - 32]));
+                        ev[u] = ex2f(__uint_as_float(c < 32 ? r0[c] : r1[c - 32]));
                     }
 #pragma unroll
                     for (int q = 0; q < NRHS; ++q) {
                         const float4 vv = *reinterpret_cast<const float4*>(v + q * TC_BN + 4 * j4);
-                        acc[q][0 % NA] = fmaf(e[0], vv.x, acc[q][0 % NA]);
-                        acc[q][1 % NA] = fmaf(e[1], vv.y, acc[q][1 % NA]);
-                        acc[q][2 % NA] = fmaf(e[2], vv.z, acc[q][2 % NA]);
-                        acc[q][3 % NA] = fmaf(e[3], vv.w, acc[q][3 % NA]);
+                        acc[q][0 % NA] = fmaf(ev[0], vv.x, acc[q][0 % NA]);
+                        acc[q][1 % NA] = fmaf(ev[1], vv.y, acc[q][1 % NA]);
+                        acc[q][2 % NA] = fmaf(ev[2], vv.z, acc[q][2 % NA]);
+                        acc[q][3 % NA] = fmaf(ev[3], vv.w, acc[q][3 % NA]);
                     }
                 }
-                tc_fence_before();
-                __syncthreads();
-                if (tid == 0 && t + TC_NS < nt) issue_load(t0 + t + TC_NS, t % TC_NS);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->s_empty[s]);   // V of this stage consumed
             }
-        }
-        if (!ok) break;   // uniform: every decision above went through __syncthreads_and
-        // combine the two column groups of each row
-        float tot[NRHS];
-#pragma unroll
-        for (int q = 0; q < NRHS; ++q) {
-            tot[q] = acc[q][0];
-#pragma unroll
-            for (int a = 1; a < NA; ++a) tot[q] += acc[q][a];
-        }
-        if (cgrp == 1) {
-#pragma unroll
-            for (int q = 0; q < NRHS; ++q) sRed[q * TC_ROWS + lrow] = tot[q];
-        }
-        __syncthreads();
-        if (cgrp == 0) {
+            if (!ok) break;
             const long long row = (long long)rb * TC_ROWS + lrow;
             if (row < nr) {
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q) {
-                    const float sum = tot[q] + sRed[q * TC_ROWS + lrow];
-                    if (part == nullptr)
-                        Q[(size_t)q * nr + row] = sum + (beta != 0.f ? beta * Vbeta[(size_t)q * ldvb + row] : 0.f);
-                    else
-                        part[((size_t)sp * NRHS + q) * nr + row] = sum;
+                    float tot = acc[q][0];
+#pragma unroll
+                    for (int a = 1; a < NA; ++a) tot += acc[q][a];
+                    part[(((size_t)sp * 2 + cgrp) * NRHS + q) * nr + row] = tot;
                 }
             }
         }
-        __syncthreads();
     }
-    if (!ok && tid == 0) {
-        atomicExch(err, 1);
-        sh->abort = 1;
-    }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (sh->abort) {
-        // let in-flight MMAs drain (bounded) before the TMEM is released
-        mbar_wait(&sh->bar_mma[0], ph_m & 1u);
-        mbar_wait(&sh->bar_mma[1], (ph_m >> 1) & 1u);
+    if (*abort) {
+        // bounded drain of MMAs that may still be in flight before the TMEM goes away
+        mbar_wait(&sh->t_full[0], 0);
+        mbar_wait(&sh->t_full[1], 0);
     }
-    __syncthreads();
+    tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
@@ -443,7 +452,7 @@ size_t tc_feature_bytes(long long n, int d) {
 }
 
 typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
-                      int, int, int, float, const float*, int, float*, float*, int*);
+                      int, int, int, float*, int*);
 
 int choose_splits_public(int nblk, int ntiles, int slots);
 
@@ -469,8 +478,7 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         KRR_TRY_CUDA(cudaMemcpy2DAsync(Vp, sizeof(float) * ncp, V + (size_t)done * nc, sizeof(float) * nc,
                                        sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
         const uint32_t tileA = 128u * Kp * 2u;
-        const size_t smem = (2 + TC_NS) * (size_t)tileA + (size_t)TC_NS * chunk * TC_BN * 4 +
-                            (size_t)TC_ROWS * chunk * 4 + 256;
+        const size_t smem = (2 + TC_NS) * (size_t)tileA + (size_t)TC_NS * chunk * TC_BN * 4 + 256;
         const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
         KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem_launch));
@@ -480,17 +488,15 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
         const int items = nrb * splits;
-        float* part = nullptr;
-        if (splits > 1) KRR_RET(bufT(ctx, "tc_part", (size_t)splits * chunk * nr, &part));
+        float* part;
+        KRR_RET(bufT(ctx, "tc_part", (size_t)2 * splits * chunk * nr, &part));
         const int grid = std::min(items, ctx->num_sms);
         fn<<<grid, TC_THREADS, smem_launch, ctx->stream>>>(FA, FB, Kp, (int)nr, (int)nc, ncp, Vp, items,
-                                                           splits, tps, beta, V + (size_t)done * nc,
-                                                           (int)nc, Q + (size_t)done * nr, part, err);
+                                                           splits, tps, part, err);
         KRR_CHECK_LAUNCH();
-        if (splits > 1) {
-            KRR_RET(launch_kmvm_reduce(ctx, part, splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
-                                       beta, Q + (size_t)done * nr, (int)nr));
-        }
+        // two column groups per split: 2 * splits partial sums per output
+        KRR_RET(launch_kmvm_reduce(ctx, part, 2 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
+                                   beta, Q + (size_t)done * nr, (int)nr));
         done += chunk;
     }
     return KRR_OK;
