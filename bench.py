@@ -161,6 +161,37 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ roofline of the product
+def roofline(p, kms, kcnt, clocks, precision, sms):
+    """ALU roofline of the kernel product (the dominant kernel of the solve).
+
+    Per pair (i, j) and right-hand side count r: the FP32 form issues d FFMA for the
+    dot product, one FADD for the norms and r FFMA on the FMA pipe plus one ex2 on the
+    MUFU; the tensor-core form moves the exponent onto tcgen05 and leaves one ex2 and
+    r FFMA.  Peak pairs/s = min(FMA-pipe rate / FMA ops per pair, MUFU rate), from
+    the SM count x 128 FP32 lanes (resp. 32 ex2 per SM per clock on GB300) x the
+    largest SM clock seen.
+    """
+    sm_max = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    ffma_rate = sms * 128 * sm_max
+    mufu_rate = sms * 32 * sm_max
+    d, nrhs = p.d, p.nrhs
+    fma_per_pair = nrhs if precision == 1 else d + 1 + nrhs
+    peak_pairs = min(ffma_rate / fma_per_pair, mufu_rate)
+    avg_s = (kms / max(kcnt, 1)) / 1e3
+    achieved = (float(p.n) * p.n / avg_s) if kcnt else None
+    name = ("k_kmvm_tc (tcgen05 BF16x3 exponent GEMM + ex2 + FFMA), (K + beta I) p" if precision == 1
+            else "k_kmvm (tiled FP32 kernel product), (K + beta I) p")
+    return {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
+            "peak": peak_pairs / 1e9, "unit": "Gpair/s",
+            "frac": (achieved / peak_pairs) if achieved else None, "traffic": None,
+            "kernel": name,
+            "peak_basis": (f"derived from unit counts x max clock ({sm_max / 1e6:.0f} MHz): "
+                           f"{sms} SMs x 128 FP32 lanes / {fma_per_pair} FMA-pipe ops per pair, "
+                           f"{sms} SMs x 32 ex2/clk"),
+            "launches": kcnt, "avg_launch_ms": avg_s * 1e3}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -186,7 +217,7 @@ def run_gpu(args):
     p = _workload(args.n, rank)
     X = torch.from_numpy(p.X).to(dev)
     Y = torch.from_numpy(p.Y).to(dev)
-    ctx = api.KRR()
+    ctx = api.KRR(precision=args.precision)
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
 
     def step():
@@ -235,23 +266,8 @@ def run_gpu(args):
     # ---- dominant kernel: the tiled kernel product of the PCG iterations
     kms, kcnt = phases["kmvm"]
     pairs = float(p.n) * p.n * p.nrhs
-    d, nrhs = p.d, p.nrhs
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
-    ffma_rate = sms * 128 * sm_max          # FP32 lanes per SM x clock
-    mufu_rate = sms * 16 * sm_max           # ex2 per SM per clock x clock
-    per_pair_fma = d + 1 + nrhs             # d FFMA (dot) + FADD (norms) + nrhs FFMA
-    peak_pairs = min(ffma_rate / per_pair_fma, mufu_rate)
-    avg_s = (kms / max(kcnt, 1)) / 1e3
-    achieved = (float(p.n) * p.n / avg_s) if kcnt else None
-    roof = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
-            "peak": peak_pairs / 1e9, "unit": "Gpair/s",
-            "frac": (achieved / peak_pairs) if achieved else None, "traffic": None,
-            "kernel": "k_kmvm (tiled FP32 kernel product, (K + beta I) p)",
-            "peak_basis": (f"recipe units x max clock: {sms} SMs x 128 FP32 lanes / "
-                           f"{per_pair_fma} FMA-pipe ops per pair vs {sms} SMs x 16 ex2; "
-                           f"{sm_max / 1e6:.0f} MHz"),
-            "launches": kcnt, "avg_launch_ms": avg_s * 1e3}
+    roof = roofline(p, kms, kcnt, clocks, args.precision,
+                    torch.cuda.get_device_properties(dev).multi_processor_count)
 
     out = None
     if rank == 0:
@@ -261,7 +277,9 @@ def run_gpu(args):
                "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32", "data": "synthetic",
                "config": {"workload": _describe(p), "l2": "flushed between steps (256 MiB write)",
-                          "precision": "FP32 kernel tiles, FP64 scalars, FP64 refinement residual",
+                          "precision": ("tensor-core BF16x3 exponent tiles (tcgen05), FP32 accumulation"
+                                        if args.precision == 1 else "FP32 kernel tiles")
+                          + "; FP64 CG scalars; float-float residual replacement",
                           "replicas": world},
                "roofline": roof, "clocks": clocks, "gpu_launches": launches,
                "mvm_pairs_per_s": pairs * kcnt / (kms / 1e3) if kcnt else None,
@@ -269,6 +287,30 @@ def run_gpu(args):
                          "mvm_count": last["mvm_count"], "rel_residual": last["rel_residual"][0],
                          "build_ms": last["build_ms"], "solve_ms": last["solve_ms"]},
                "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items() if v[1]}}
+
+    # ---- the other precision form on the same workload and tolerance (reported beside)
+    if not args.no_other_form:
+        other = 1 - args.precision
+        ctx2 = api.KRR(precision=other)
+        ctx2.build(X, p.sigma, p.beta, p.k, seed=1)
+        ctx2.solve(Y, tol=p.tol)
+        torch.cuda.synchronize()
+        ctx2.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx2.build(X, p.sigma, p.beta, p.k, seed=1)
+        _, inf2 = ctx2.solve(Y, tol=p.tol)
+        e1.record(stream)
+        e1.synchronize()
+        ph2 = ctx2.phase_times()
+        ctx2.close()
+        if out is not None:
+            out["other_form"] = {
+                "precision": "FP32 kernel tiles" if other == 0 else "tensor-core tiles",
+                "seconds": e0.elapsed_time(e1) / 1e3, "iters": inf2["iters"],
+                "rel_residual": inf2["rel_residual"][0],
+                "kmvm_avg_ms": ph2["kmvm"][0] / max(ph2["kmvm"][1], 1)}
 
     # ---- end to end through the public API with host buffers
     if not args.no_e2e:
@@ -280,7 +322,7 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            a, _ = api.solve(Xh, Yh, p.sigma, p.beta, p.k, seed=1, tol=p.tol)
+            a, _ = api.solve(Xh, Yh, p.sigma, p.beta, p.k, seed=1, tol=p.tol, precision=args.precision)
             e1.record()
             e1.synchronize()
             if s:
@@ -320,6 +362,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-form", action="store_true")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="kernel product: 0 FP32 tiles, 1 tensor-core tiles (default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -105,6 +105,52 @@ def test_solve_with_fp64_residual_mode(K):
     assert np.linalg.norm(alpha.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-5
 
 
+# ------------------------------------------------------------------ tensor-core product
+def test_tc_descriptor_known_answer():
+    from paper_1905_10587_gb300 import api
+    bad, err = api.tc_selftest(0)
+    assert bad == 0 and err == 0.0
+    bad1, _ = api.tc_selftest(1)   # the swapped stride convention must be detected
+    assert bad1 > 0
+
+
+@pytest.mark.parametrize("n,d,nrhs,beta", [(2000, 4, 1, 1e-2), (1, 3, 1, 0.5), (127, 2, 3, 0.0),
+                                            (1000, 8, 16, 1e-3), (777, 13, 5, 0.1),
+                                            (300, 16, 2, 0.0), (4099, 3, 1, 1e-4)])
+def test_kmvm_tensor_core_square(K, n, d, nrhs, beta):
+    rng = np.random.Generator(np.random.PCG64(n + d))
+    X = rng.uniform(-2, 2, size=(n, d)).astype(np.float32)
+    V = rng.normal(size=(n, nrhs)).astype(np.float32)
+    sigma = 0.3 * np.sqrt(d)
+    ctx = K(precision=1)
+    Q = ctx.kmvm(_t(X), _t(X), _t(V), sigma, beta).cpu().numpy()
+    ref = O.kmvm(X, V.astype(np.float64), sigma, beta)
+    assert _relcols(Q, ref).max() <= 1e-5
+
+
+def test_kmvm_tensor_core_rectangular_full_size(K):
+    p = synth.mixture()
+    rng = np.random.Generator(np.random.PCG64(6))
+    Xt = p.X[rng.choice(p.n, 3000, replace=False)] + 0.1
+    ctx = K(precision=1)
+    Q = ctx.kmvm(_t(Xt), _t(p.X), _t(p.Y), p.sigma).cpu().numpy()
+    rows = rng.choice(len(Xt), 200, replace=False)
+    ref = O.kmvm_rect(Xt[rows], p.X, p.Y.astype(np.float64), p.sigma)
+    assert _relcols(Q[rows], ref).max() <= 1e-5
+
+
+def test_solve_tensor_core_vs_dense(K):
+    p = synth.small()
+    ctx = K(precision=1)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
+    alpha, info = ctx.solve(_t(p.Y), tol=p.tol)
+    a = alpha.cpu().numpy()
+    ref = O.solve_dense(p.X, p.Y.astype(np.float64), p.sigma, p.beta)
+    r = O.residual(p.X, a, p.Y, p.sigma, p.beta)
+    assert np.linalg.norm(r) / np.linalg.norm(p.Y) <= 1e-6
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= 1e-4
+
+
 # ------------------------------------------------------------------ Algorithm 1
 def test_omega_matches_oracle_generator(K):
     ctx = K()
@@ -220,9 +266,10 @@ def test_solve_multi_rhs_and_predict(K):
     assert np.all(np.abs(f - fref) <= 1e-5 * cond)
 
 
-def test_solve_full_size_mixture_sampled_residual(K):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_full_size_mixture_sampled_residual(K, precision):
     p = synth.mixture()
-    ctx = K()
+    ctx = K(precision=precision)
     ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
     alpha, info = ctx.solve(_t(p.Y), tol=p.tol)
     a = alpha.cpu().numpy()
