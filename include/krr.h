@@ -198,6 +198,27 @@ int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out);
 int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol,
               double* alpha, krr_solve_info* info);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free kernel product.  The paper has no counterpart: this entry
+ * exists for callers that may not allocate device memory, such as an
+ * application that owns all GPU memory through its own pool, or code running
+ * where a cudaMalloc is not allowed.  It computes the same product as krr_kmvm
+ * (FP32 tiles; no context needed), taking all temporaries from one fixed device
+ * array of KRR_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps
+ * until the process exits.  The first call on a device looks up that array's
+ * device address, so make that first call before any stream capture.  Calls
+ * share the array: calls whose work overlaps on the GPU (other streams, other
+ * threads) race on it and must be serialised by the caller.  No temporary needs
+ * to start at zero.  If a size needs more scratch than the array holds, nothing
+ * is launched, KRR_E_NOMEM is returned and *scratch_needed (if non-NULL) says how
+ * many bytes it would take; bad arguments return KRR_E_INVAL.  All pointers are
+ * device pointers as for krr_kmvm; stream is a cudaStream_t (NULL = default).
+ * ------------------------------------------------------------------------- */
+#define KRR_NOALLOC_SCRATCH_BYTES (64u << 20)
+int krr_kmvm_noalloc(const float* Xr, long long nr, const float* Xc, long long nc, int d,
+                     double sigma, double beta, const float* V, int nrhs, float* Q, void* stream,
+                     unsigned long long* scratch_needed);
+
 /* f = K(Xtest, X) alpha (Eq. (1)); Xtest m x d, alpha n x nrhs FP32, f m x nrhs. */
 int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alpha, int nrhs,
                 float* f);

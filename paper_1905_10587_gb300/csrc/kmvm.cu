@@ -341,6 +341,87 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
     return KRR_OK;
 }
 
+// ------------------------------------------------------------------ product into given scratch
+// The FP32 product K(Xr, Xc) V + beta V with every temporary (mean, packed points,
+// split-K partial sums) carved from one caller-provided device buffer: no device
+// allocation and no context.  Returns KRR_E_INVAL with *needed set when the buffer
+// is too small.
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long long nr,
+                      const float* Xc, long long nc, int d, double sigma, double beta,
+                      const float* V, int nrhs, float* Q, unsigned char* scratch, size_t cap,
+                      size_t* needed) {
+    const int dk = kernel_dim(d), ps = packed_stride(d);
+    const bool same = (Xr == Xc && nr == nc);
+    const int nblk_mean = (int)std::min<long long>(2LL * num_sms, ceil_div(nc, 256));
+    // split-K layout of every right-hand-side chunk, as the context path chooses it
+    size_t part_floats = 0;
+    for (int done = 0; done < nrhs;) {
+        const int left = nrhs - done;
+        const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        int R = 4;
+        kmvm_fn fn = pick(dk, chunk, &R);
+        if (!fn) return KRR_E_INVAL;
+        int occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, KM_THREADS, 0) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
+        const int nblk = (int)ceil_div(nr, KM_THREADS * R);
+        const int ntiles = (int)ceil_div(nc, KM_BN);
+        int splits = choose_splits(nblk, ntiles, num_sms * occ);
+        const int tps = (ntiles + splits - 1) / splits;
+        splits = (ntiles + tps - 1) / tps;
+        if (splits > 1) part_floats = std::max(part_floats, (size_t)splits * chunk * (size_t)nr);
+        done += chunk;
+    }
+    const size_t off_mpart = 0;
+    const size_t off_mu = off_mpart + align256(sizeof(double) * nblk_mean * d);
+    const size_t off_pc = off_mu + align256(sizeof(double) * d);
+    const size_t off_pr = off_pc + align256(sizeof(float) * (size_t)nc * ps);
+    const size_t off_part = off_pr + (same ? 0 : align256(sizeof(float) * (size_t)nr * ps));
+    const size_t total = off_part + align256(sizeof(float) * part_floats);
+    if (needed) *needed = total;
+    if (total > cap) return KRR_E_INVAL;
+
+    double* mpart = reinterpret_cast<double*>(scratch + off_mpart);
+    double* mu = reinterpret_cast<double*>(scratch + off_mu);
+    float* Pc = reinterpret_cast<float*>(scratch + off_pc);
+    float* Pr = same ? Pc : reinterpret_cast<float*>(scratch + off_pr);
+    float* part = reinterpret_cast<float*>(scratch + off_part);
+    const double s = 1.4426950408889634 / (2.0 * sigma * sigma);
+    k_mean_partial<<<nblk_mean, 256, 0, stream>>>(Xc, nc, d, mpart);
+    k_mean_final<<<1, 64, 0, stream>>>(mpart, nblk_mean, d, nc, mu);
+    k_pack<<<ceil_div(nc, 256), 256, 0, stream>>>(Xc, nc, d, dk, ps, mu, std::sqrt(s), Pc);
+    if (!same) k_pack<<<ceil_div(nr, 256), 256, 0, stream>>>(Xr, nr, d, dk, ps, mu, std::sqrt(s), Pr);
+    for (int done = 0; done < nrhs;) {
+        const int left = nrhs - done;
+        const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        int R = 4;
+        kmvm_fn fn = pick(dk, chunk, &R);
+        int occ = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, KM_THREADS, 0) !=
+                cudaSuccess || occ < 1)
+            occ = 1;
+        const int nblk = (int)ceil_div(nr, KM_THREADS * R);
+        const int ntiles = (int)ceil_div(nc, KM_BN);
+        int splits = choose_splits(nblk, ntiles, num_sms * occ);
+        const int tps = (ntiles + splits - 1) / splits;
+        splits = (ntiles + tps - 1) / tps;
+        const float* Vc = V + (size_t)done * nc;
+        float* Qc = Q + (size_t)done * nr;
+        fn<<<dim3(nblk, splits), KM_THREADS, 0, stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps,
+                                                          (float)beta, Qc, (int)nr,
+                                                          splits > 1 ? part : nullptr);
+        if (splits > 1)
+            k_kmvm_reduce<<<ceil_div(nr * chunk, 256), 256, 0, stream>>>(part, splits, (int)nr, chunk,
+                                                                          Vc, (int)nc, (float)beta,
+                                                                          Qc, (int)nr);
+        done += chunk;
+    }
+    return cudaGetLastError() == cudaSuccess ? KRR_OK : KRR_E_CUDA;
+}
+
 // ------------------------------------------------------------------ FP64 residual
 constexpr int HP_THREADS = 128;
 constexpr int HP_BN = 64;
