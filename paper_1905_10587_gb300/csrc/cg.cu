@@ -134,17 +134,20 @@ k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restr
             __syncthreads();
             if (c4 < ld4) {
                 const float4* fp = F4 + b0 * ld4 + c4;
+                constexpr int U = 8;   // rows whose loads are in flight together
                 int i = 0;
-                for (; i + 2 <= nb; i += 2) {
-                    const float4 f0 = fp[(size_t)(i + 0) * ld4];
-                    const float4 f1 = fp[(size_t)(i + 1) * ld4];
+                for (; i + U <= nb; i += U) {
+                    float4 f[U];
 #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        const float a0 = sr[q][i], a1 = sr[q][i + 1];
-                        ff_acc(hx[q], lx[q], f0.x, a0); ff_acc(hy[q], ly[q], f0.y, a0);
-                        ff_acc(hz[q], lz[q], f0.z, a0); ff_acc(hw[q], lw[q], f0.w, a0);
-                        ff_acc(hx[q], lx[q], f1.x, a1); ff_acc(hy[q], ly[q], f1.y, a1);
-                        ff_acc(hz[q], lz[q], f1.z, a1); ff_acc(hw[q], lw[q], f1.w, a1);
+                    for (int u = 0; u < U; ++u) f[u] = fp[(size_t)(i + u) * ld4];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            const float a = sr[q][i + u];
+                            ff_acc(hx[q], lx[q], f[u].x, a); ff_acc(hy[q], ly[q], f[u].y, a);
+                            ff_acc(hz[q], lz[q], f[u].z, a); ff_acc(hw[q], lw[q], f[u].w, a);
+                        }
                     }
                 }
                 for (; i < nb; ++i) {
