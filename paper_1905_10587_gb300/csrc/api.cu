@@ -387,17 +387,32 @@ int krr_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, float* 
 }
 
 static int sketch_internal(krr_ctx* ctx, long long n, int l, unsigned long long seed, float** Yout,
-                           int* ldy) {
+                           int* ldy, bool tensor_cores) {
     const int ld = (l + 3) / 4 * 4;
-    float *Om, *Y;
-    KRR_RET(bufT(ctx, "omega", (size_t)n * ld, &Om));
+    float* Y;
     KRR_RET(bufT(ctx, "sketch", (size_t)n * ld, &Y));
-    {
-        Phase ph(ctx, PH_OMEGA);
-        KRR_RET(launch_omega(ctx, seed, l, n, ld, Om));
+    if (tensor_cores && ctx->FA) {
+        // BF16 Omega in tensor-core tiles and the two-MMA sketch
+        const long long npad = (n + 255) / 256 * 256;
+        const int nab = (l + 255) / 256, njc_alloc = (int)(npad / 64);
+        void* Om;
+        KRR_RET(buf(ctx, "omega_bf16", (size_t)nab * 256 * npad * 2, &Om));
+        {
+            Phase ph(ctx, PH_OMEGA);
+            KRR_RET(launch_omega_bf16_tiled(ctx, seed, l, n, nab, njc_alloc, Om));
+        }
+        Phase ph(ctx, PH_SKETCH);
+        KRR_RET(launch_sketch_tc(ctx, ctx->FA, ctx->FB, n, ctx->d, Om, l, njc_alloc, Y, ld));
+    } else {
+        float* Om;
+        KRR_RET(bufT(ctx, "omega", (size_t)n * ld, &Om));
+        {
+            Phase ph(ctx, PH_OMEGA);
+            KRR_RET(launch_omega(ctx, seed, l, n, ld, Om));
+        }
+        Phase ph(ctx, PH_SKETCH);
+        KRR_RET(launch_kgemm(ctx, ctx->P, n, ctx->P, n, ctx->d, Om, ld, ld, Y, ld));
     }
-    Phase ph(ctx, PH_SKETCH);
-    KRR_RET(launch_kgemm(ctx, ctx->P, n, ctx->P, n, ctx->d, Om, ld, ld, Y, ld));
     *Yout = Y;
     *ldy = ld;
     return KRR_OK;
@@ -413,7 +428,7 @@ int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, i
     KRR_RET(build_common(ctx, X, n, d, sigma, 1.0));
     float* Yi;
     int ld;
-    KRR_RET(sketch_internal(ctx, n, l, seed, &Yi, &ld));
+    KRR_RET(sketch_internal(ctx, n, l, seed, &Yi, &ld, false));
     KRR_TRY_CUDA(cudaMemcpy2DAsync(Y, sizeof(float) * l, Yi, sizeof(float) * ld, sizeof(float) * l,
                                    n, cudaMemcpyDeviceToDevice, ctx->stream));
     return KRR_OK;
@@ -440,7 +455,7 @@ int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double s
     ctx->l = l;
     float* Y;
     int ld;
-    KRR_RET(sketch_internal(ctx, n, l, seed, &Y, &ld));
+    KRR_RET(sketch_internal(ctx, n, l, seed, &Y, &ld, true));
     int* piv;
     float* rdiag;
     KRR_RET(bufT(ctx, "piv", (size_t)k, &piv));
@@ -452,7 +467,14 @@ int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double s
     std::vector<float> rd(k);
     KRR_TRY_CUDA(cudaMemcpyAsync(rd.data(), rdiag, sizeof(float) * k, cudaMemcpyDeviceToHost,
                                  ctx->stream));
+    int tc_err = 0;
+    if (ctx->FA) {
+        int* err;
+        KRR_RET(bufT(ctx, "tc_err", 1, &err));
+        KRR_TRY_CUDA(cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    }
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (tc_err) return fail(ctx, KRR_E_CUDA, "tensor-core sketch: a bounded wait timed out");
     int k_eff = 0;
     const float thr = (float)(ctx->opts.anchor_rtol * rd[0]);
     while (k_eff < k && rd[k_eff] > thr && std::isfinite(rd[k_eff])) ++k_eff;

@@ -59,11 +59,12 @@ k_dot64_part(const double* __restrict__ A, const double* __restrict__ B, long lo
 }
 
 __global__ void k_sum_parts(const double* __restrict__ part, int nblk, int nrhs, double* out) {
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= nrhs) return;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
-    out[q] = s;
+    for (int b = lane; b < nblk; b += 32) s += part[(size_t)q * nblk + b];
+    s = warp_sum(s);
+    if (lane == 0) out[q] = s;
 }
 
 int launch_dot(krr_ctx* ctx, const float* A, const float* B, long long n, int nrhs, double* out) {
@@ -72,7 +73,7 @@ int launch_dot(krr_ctx* ctx, const float* A, const float* B, long long n, int nr
     KRR_RET(bufT(ctx, "dot_part", (size_t)nb * nrhs, &part));
     k_dot_part<<<nb, VT, 0, ctx->stream>>>(A, B, n, nrhs, part);
     KRR_CHECK_LAUNCH();
-    k_sum_parts<<<1, 32, 0, ctx->stream>>>(part, nb, nrhs, out);
+    k_sum_parts<<<1, 32 * nrhs, 0, ctx->stream>>>(part, nb, nrhs, out);
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }
@@ -83,7 +84,7 @@ int launch_dot64(krr_ctx* ctx, const double* A, const double* B, long long n, in
     KRR_RET(bufT(ctx, "dot_part", (size_t)nb * nrhs, &part));
     k_dot64_part<<<nb, VT, 0, ctx->stream>>>(A, B, n, nrhs, part);
     KRR_CHECK_LAUNCH();
-    k_sum_parts<<<1, 32, 0, ctx->stream>>>(part, nb, nrhs, out);
+    k_sum_parts<<<1, 32 * nrhs, 0, ctx->stream>>>(part, nb, nrhs, out);
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }
@@ -236,28 +237,51 @@ k_gemv_n_apply(const float* __restrict__ F, long long n, int k, int ldF, const d
     double rz[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) rz[q] = 0.0;
-    for (long long i = (long long)blockIdx.x * (VT / 32) + w; i < n; i += (long long)gridDim.x * (VT / 32)) {
-        float s[NQ];
+    // each warp takes two rows at a time and issues all of their loads before the FMAs
+    const long long wstride = (long long)gridDim.x * (VT / 32);
+    for (long long i0 = (long long)blockIdx.x * (VT / 32) + w; i0 < n; i0 += 2 * wstride) {
+        const long long i1 = i0 + wstride;
+        const bool has1 = i1 < n;
+        float s0[NQ], s1[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) s[q] = 0.f;
-        const float4* fr = F4 + i * ld4;
-#pragma unroll 4
-        for (int c4 = lane; c4 < ld4; c4 += 32) {
-            const float4 f = fr[c4];
+        for (int q = 0; q < NQ; ++q) s0[q] = s1[q] = 0.f;
+        const float4* f0 = F4 + i0 * ld4;
+        const float4* f1 = F4 + (has1 ? i1 : i0) * ld4;
+        for (int c0 = lane; c0 < ld4; c0 += 32 * 4) {
+            float4 a[4], b[4];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const float4 vv = sv4[q * ld4 + c4];
-                s[q] = fmaf(f.x, vv.x, fmaf(f.y, vv.y, fmaf(f.z, vv.z, fmaf(f.w, vv.w, s[q]))));
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 32 * u;
+                a[u] = c < ld4 ? f0[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                b[u] = (c < ld4 && has1) ? f1[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 32 * u;
+                if (c >= ld4) break;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const float4 vv = sv4[q * ld4 + c];
+                    s0[q] = fmaf(a[u].x, vv.x, fmaf(a[u].y, vv.y, fmaf(a[u].z, vv.z, fmaf(a[u].w, vv.w, s0[q]))));
+                    s1[q] = fmaf(b[u].x, vv.x, fmaf(b[u].y, vv.y, fmaf(b[u].z, vv.z, fmaf(b[u].w, vv.w, s1[q]))));
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            const float t = warp_sum(s[q]);
+            const float t0 = warp_sum(s0[q]);
+            const float t1 = warp_sum(s1[q]);
             if (lane == 0) {
-                const float r = R[q * ldr + i];
-                const float z = (r - t) * inv_beta;
-                Z[q * ldr + i] = z;
-                rz[q] += (double)r * (double)z;
+                const float r0 = R[q * ldr + i0];
+                const float z0 = (r0 - t0) * inv_beta;
+                Z[q * ldr + i0] = z0;
+                rz[q] += (double)r0 * (double)z0;
+                if (has1) {
+                    const float r1 = R[q * ldr + i1];
+                    const float z1 = (r1 - t1) * inv_beta;
+                    Z[q * ldr + i1] = z1;
+                    rz[q] += (double)r1 * (double)z1;
+                }
             }
         }
     }
@@ -312,12 +336,21 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
 }
 
 // ------------------------------------------------------------------ PCG recurrences
+// The scalar kernels run one warp per right-hand side: the warp sums that column's
+// per-block partials (FP64) and lane 0 applies the recurrence.
+__device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part, int nblk, int q) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[(size_t)q * nblk + b];
+    return warp_sum(s);
+}
+
 // a_q = rz_q / (p_q . q_q) for active columns; zero otherwise.
 __global__ void k_cg_alpha(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs) {
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5;
     if (q >= nrhs) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
+    const double s = warp_sum_parts(part, nblk, q);
+    if ((threadIdx.x & 31) != 0) return;
     cg->pq[q] = s;
     double a = 0.0;
     if (cg->active[q]) {
@@ -356,17 +389,18 @@ __global__ void k_cg_check(CGScalars* cg, const double* __restrict__ part, int n
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5;
     if (q < nrhs) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
-        cg->rr[q] = s;
-        if (!isfinite(s)) {
-            cg->bad = 1;
-            cg->active[q] = 0;
+        const double s = warp_sum_parts(part, nblk, q);
+        if ((threadIdx.x & 31) == 0) {
+            cg->rr[q] = s;
+            if (!isfinite(s)) {
+                cg->bad = 1;
+                cg->active[q] = 0;
+            }
+            if (tol2 > 0.0 && cg->active[q] && !(s > tol2 * cg->rr0[q])) cg->active[q] = 0;
+            if (cg->active[q]) atomicOr(&any, 1);
         }
-        if (tol2 > 0.0 && cg->active[q] && !(s > tol2 * cg->rr0[q])) cg->active[q] = 0;
-        if (cg->active[q]) atomicOr(&any, 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) cg->all_done = any ? 0 : 1;
@@ -374,10 +408,10 @@ __global__ void k_cg_check(CGScalars* cg, const double* __restrict__ part, int n
 
 // b_q = rz_new / rz; rz = rz_new (b = 0 for finished columns: p restarts from z)
 __global__ void k_cg_beta(CGScalars* cg, const double* __restrict__ part, int nblk, int nrhs) {
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5;
     if (q >= nrhs) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)q * nblk + b];
+    const double s = warp_sum_parts(part, nblk, q);
+    if ((threadIdx.x & 31) != 0) return;
     const double rz = cg->rz[q];
     cg->b[q] = (cg->active[q] && rz != 0.0 && isfinite(s)) ? s / rz : 0.0;
     cg->rz[q] = s;
@@ -456,7 +490,7 @@ int launch_cg_alpha(krr_ctx* ctx, const float* p, const float* q, int nrhs, doub
     const int nb = vec_blocks(ctx, ctx->n);
     k_dot_part<<<nb, VT, 0, ctx->stream>>>(p, q, ctx->n, nrhs, part);
     KRR_CHECK_LAUNCH();
-    k_cg_alpha<<<1, 32, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs);
+    k_cg_alpha<<<1, 32 * nrhs, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs);
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }
@@ -466,14 +500,14 @@ int launch_cg_update_xr(krr_ctx* ctx, float* x, float* r, const float* p, const 
     const int nb = vec_blocks(ctx, ctx->n);
     k_cg_update_xr<<<nb, VT, 0, ctx->stream>>>(x, r, p, q, ctx->n, nrhs, ctx->cg, part);
     KRR_CHECK_LAUNCH();
-    k_cg_check<<<1, 32, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs, tol2);
+    k_cg_check<<<1, 32 * nrhs, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs, tol2);
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }
 
 int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const double* rz_part) {
     const int nb = vec_blocks(ctx, ctx->n);
-    k_cg_beta<<<1, 32, 0, ctx->stream>>>(ctx->cg, rz_part, nb, nrhs);
+    k_cg_beta<<<1, 32 * nrhs, 0, ctx->stream>>>(ctx->cg, rz_part, nb, nrhs);
     KRR_CHECK_LAUNCH();
     k_cg_update_p<<<nb, VT, 0, ctx->stream>>>(p, z, ctx->n, nrhs, ctx->cg);
     KRR_CHECK_LAUNCH();

@@ -183,6 +183,10 @@ size_t tc_feature_bytes(long long n, int d);
 int launch_tc_features(krr_ctx* ctx, const float* P, long long n, int d, int role, unsigned char* out);
 int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
                    long long nc, int d, float beta, const float* V, int nrhs, float* Q);
+int launch_sketch_tc(krr_ctx* ctx, const unsigned char* FA, const unsigned char* FB, long long n, int d,
+                     const void* Om, int l, int njc_alloc, float* Y, int ldy);
+int launch_omega_bf16_tiled(krr_ctx* ctx, unsigned long long seed, int l, long long n, int nab,
+                            int njc, void* out);
 
 // residual_ff.cu: same contract in float-float on the FP32 pipe (d <= 16; else FP64)
 int launch_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,

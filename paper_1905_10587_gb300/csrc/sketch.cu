@@ -9,6 +9,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <cuda_bf16.h>
 
 namespace krr {
 
@@ -73,6 +74,50 @@ __global__ void k_omega_exact(unsigned long long seed, int l, long long n, float
     sincospif(2.f * u2, &sn, &cs);
     OmT[j * l + 2 * c] = rad * cs;
     if (2 * c + 1 < l) OmT[j * l + 2 * c + 1] = rad * sn;
+}
+
+// The same Omega rounded to BF16 and laid out for the tensor-core sketch: tiles of
+// 256 projections x 64 points in the core-matrix order (8 rows x 16 bytes per
+// 128-byte block; row = projection a, K = point j), tile (ab, jc) at byte offset
+// (ab * njc + jc) * 32 KB.  Entries with a >= l or j >= n are zero.
+__global__ void k_omega_bf16_tiled(unsigned long long seed, int l, long long n, int nab, int njc,
+                                   __nv_bfloat16* __restrict__ out) {
+    const long long npad = (long long)njc * 64;
+    const int half = nab * 128;                       // pairs of projections
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npad * half) return;
+    const long long j = e / half;
+    const int c = (int)(e - j * half);
+    float z0 = 0.f, z1 = 0.f;
+    if (j < n && 2 * c < l) {
+        const uint4 r = philox4x32_10(
+            make_uint4((unsigned)(j & 0xffffffffu), (unsigned)(j >> 32), (unsigned)c, 0u),
+            make_uint2((unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)));
+        const float u1 = (float)((r.x >> 8) + 1u) * 0x1p-24f;
+        const float u2 = (float)(r.y >> 8) * 0x1p-24f;
+        const float rad = sqrtf(-2.f * logf(u1));
+        float sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        z0 = rad * cs;
+        z1 = (2 * c + 1 < l) ? rad * sn : 0.f;
+    }
+    const int jc = (int)(j >> 6), jl = (int)(j & 63);
+    for (int u = 0; u < 2; ++u) {
+        const int a = 2 * c + u;
+        const int ab = a >> 8, al = a & 255;
+        const size_t tile = ((size_t)ab * njc + jc) * (256 * 64);
+        const size_t off = (size_t)(((al >> 3) * 8 + (jl >> 3)) * 64 + (al & 7) * 8 + (jl & 7));
+        out[tile + off] = __float2bfloat16_rn(u ? z1 : z0);
+    }
+}
+
+int launch_omega_bf16_tiled(krr_ctx* ctx, unsigned long long seed, int l, long long n, int nab,
+                            int njc, void* out) {
+    const long long tot = (long long)njc * 64 * nab * 128;
+    k_omega_bf16_tiled<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(seed, l, n, nab, njc,
+                                                                    static_cast<__nv_bfloat16*>(out));
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
 }
 
 int launch_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, int ld, float* OmT) {

@@ -434,8 +434,235 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// ------------------------------------------------------------------ tensor-core sketch
+// Y = K Omega^T for Algorithm 1, as two chained tcgen05 MMAs per 64-point chunk j:
+//   MMA1  S(128 x 64)  = FA(rows) . FB(chunk)^T      (exponents, TMEM, 2 buffers)
+//   epilogue: P = bf16(2^S) into shared memory in core-matrix order (2 buffers)
+//   MMA2  C(128 x 256) += P . Omega(256 projections x chunk)^T   (TMEM, 256 columns)
+// A work item is (128-row tile, block of 256 projections); the C tile is written to Y
+// at the end of the item.  Roles: warp 0 bulk copies, warp 1 MMAs, warps 2..9 epilogue.
+// BF16 P and Omega only perturb the sketch (about 4e-3 relative), which only steers
+// the anchor choice.
+constexpr int SK_EPI = 8;
+constexpr int SK_THREADS = 32 * (2 + SK_EPI);
+constexpr int SK_NS = 3;
+constexpr int SK_JC = 64;            // points per chunk
+constexpr int SK_NB = 256;           // projections per block
+constexpr uint32_t SK_OMT = SK_NB * SK_JC * 2;   // bytes of one Omega tile
+
+struct SkShared {
+    uint64_t a_full, a_empty, s_full[SK_NS], s_empty[SK_NS], x_full[2], x_empty[2], p_full[2],
+        p_empty[2], c_full, c_empty;
+    uint32_t tbase;
+    int abort;
+};
+
+__global__ void __launch_bounds__(SK_THREADS, 1)
+k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB,
+            const unsigned char* __restrict__ Om, int Kp, int n, int nab, int njc, int njc_alloc,
+            int items, float* __restrict__ Y, int ldy, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t tileA = 128u * Kp * 2u;
+    const uint32_t tileB1 = (uint32_t)SK_JC * Kp * 2u;
+    unsigned char* sA = smem;
+    unsigned char* sB1 = sA + tileA;                        // SK_NS x tileB1
+    unsigned char* sB2 = sB1 + SK_NS * tileB1;              // SK_NS x SK_OMT
+    unsigned char* sP = sB2 + SK_NS * SK_OMT;               // 2 x (128 x 64 bf16)
+    SkShared* sh = reinterpret_cast<SkShared*>(sP + 2 * 128 * SK_JC * 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&sh->a_full, 1);
+        mbar_init(&sh->a_empty, 1);
+        for (int s = 0; s < SK_NS; ++s) {
+            mbar_init(&sh->s_full[s], 1);
+            mbar_init(&sh->s_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->x_full[b], 1);
+            mbar_init(&sh->x_empty[b], SK_EPI);
+            mbar_init(&sh->p_full[b], SK_EPI);
+            mbar_init(&sh->p_empty[b], 1);
+        }
+        mbar_init(&sh->c_full, 1);
+        mbar_init(&sh->c_empty, SK_EPI);
+        sh->abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) tmem_alloc(&sh->tbase, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tbase;            // S buffers at columns 0 and 64, C at 256
+    volatile int* abort = &sh->abort;
+    auto give_up = [&]() {
+        *abort = 1;
+        atomicExch(err, 1);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {   // ------------------------------------------------ producer
+            uint32_t g = 0, ic = 0;
+            for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
+                const int rt = item / nab, ab = item - rt * nab;
+                if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u)) { give_up(); break; }
+                mbar_expect_tx(&sh->a_full, tileA);
+                bulk_g2s(sA, FA + (size_t)rt * tileA, tileA, &sh->a_full);
+                for (int jc = 0; jc < njc; ++jc, ++g) {
+                    const int s = g % SK_NS;
+                    if (!mbar_wait(&sh->s_empty[s], ((g / SK_NS) & 1u) ^ 1u)) { give_up(); break; }
+                    mbar_expect_tx(&sh->s_full[s], tileB1 + SK_OMT);
+                    bulk_g2s(sB1 + s * tileB1, FB + (size_t)jc * tileB1, tileB1, &sh->s_full[s]);
+                    bulk_g2s(sB2 + s * SK_OMT, Om + ((size_t)ab * njc_alloc + jc) * SK_OMT, SK_OMT,
+                             &sh->s_full[s]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ------------------------------------------------ MMA issuer
+            const uint32_t id1 = idesc_bf16(128, SK_JC), id2 = idesc_bf16(128, SK_NB);
+            const uint32_t sbo1 = (uint32_t)Kp * 16u, sbo2 = SK_JC * 16u;
+            uint32_t g = 0, ic = 0;
+            auto mma1 = [&](uint32_t gg) -> bool {      // exponents of chunk gg into S[gg & 1]
+                const int s = gg % SK_NS, b = gg & 1;
+                if (!mbar_wait(&sh->s_full[s], (gg / SK_NS) & 1u)) return false;
+                if (!mbar_wait(&sh->x_empty[b], ((gg >> 1) & 1u) ^ 1u)) return false;
+                tc_fence_after();
+                const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(sB1 + s * tileB1);
+                for (int kk = 0; kk < Kp / 16; ++kk)
+                    mma_bf16(tmem + (uint32_t)(b * SK_JC), smem_desc(a_addr + kk * 256u, 128u, sbo1),
+                             smem_desc(b_addr + kk * 256u, 128u, sbo1), id1, kk > 0 ? 1u : 0u);
+                mma_commit(&sh->x_full[b]);
+                return true;
+            };
+            for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
+                if (!mbar_wait(&sh->a_full, ic & 1u)) { give_up(); break; }
+                const uint32_t g0 = g;
+                bool ok = mma1(g0);
+                for (int jc = 0; jc < njc && ok; ++jc) {
+                    const uint32_t gg = g0 + jc;
+                    if (jc + 1 < njc) ok = mma1(gg + 1);
+                    else mma_commit(&sh->a_empty);          // last exponent MMA of the item
+                    if (!ok) break;
+                    const int s = gg % SK_NS, b = gg & 1;
+                    if (!mbar_wait(&sh->p_full[b], (gg >> 1) & 1u)) { ok = false; break; }
+                    if (jc == 0 && !mbar_wait(&sh->c_empty, (ic & 1u) ^ 1u)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t p_addr = smem_u32(sP + b * 128 * SK_JC * 2);
+                    const uint32_t o_addr = smem_u32(sB2 + s * SK_OMT);
+                    for (int kk = 0; kk < SK_JC / 16; ++kk)
+                        mma_bf16(tmem + 256u, smem_desc(p_addr + kk * 256u, 128u, sbo2),
+                                 smem_desc(o_addr + kk * 256u, 128u, sbo2), id2,
+                                 (jc > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&sh->p_empty[b]);
+                    mma_commit(&sh->s_empty[s]);
+                    if (jc == njc - 1) mma_commit(&sh->c_full);
+                }
+                g = g0 + njc;
+                if (!ok) { give_up(); break; }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int e = warp - 2;
+        const int quarter = warp & 3, cg = e >> 2;   // cg: which 32 of the 64 S columns
+        const int r = quarter * 32 + lane;             // row inside the 128-row tile
+        uint32_t g = 0, ic = 0;
+        for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
+            const int rt = item / nab, ab = item - rt * nab;
+            bool ok = true;
+            for (int jc = 0; jc < njc; ++jc, ++g) {
+                const int b = g & 1;
+                ok = mbar_wait(&sh->x_full[b], (g >> 1) & 1u) && mbar_wait(&sh->p_empty[b], ((g >> 1) & 1u) ^ 1u);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) { if (lane == 0) give_up(); break; }
+                tc_fence_after();
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * SK_JC + cg * 32), v);
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->x_empty[b]);
+                unsigned char* pb = sP + b * 128 * SK_JC * 2;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {   // 8 consecutive K = one core-matrix row
+                    uint32_t w[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const float e0 = ex2f(__uint_as_float(v[8 * u + 2 * h]));
+                        const float e1 = ex2f(__uint_as_float(v[8 * u + 2 * h + 1]));
+                        const __nv_bfloat162 pr = __floats2bfloat162_rn(e0, e1);
+                        w[h] = *reinterpret_cast<const uint32_t*>(&pr);
+                    }
+                    *reinterpret_cast<uint4*>(pb + tile_off(r, cg * 32 + 8 * u, SK_JC)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->p_full[b]);
+            }
+            if (!ok) break;
+            // the item's C tile: this warp's 32 rows, 128 of the 256 projections
+            ok = __all_sync(0xffffffffu, mbar_wait(&sh->c_full, ic & 1u));
+            if (!ok) { if (lane == 0) give_up(); break; }
+            tc_fence_after();
+            const long long row = (long long)rt * 128 + r;
+            for (int u = 0; u < 4; ++u) {
+                uint32_t cv[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(256 + cg * 128 + 32 * u), cv);
+                tmem_wait_ld();
+                const int a0 = ab * SK_NB + cg * 128 + 32 * u;
+                if (row < n) {
+                    float4* dst = reinterpret_cast<float4*>(Y + (size_t)row * ldy + a0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (a0 + 4 * q < ldy)
+                            dst[q] = make_float4(__uint_as_float(cv[4 * q]), __uint_as_float(cv[4 * q + 1]),
+                                                 __uint_as_float(cv[4 * q + 2]), __uint_as_float(cv[4 * q + 3]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->c_empty);
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (*abort) {
+        mbar_wait(&sh->c_full, 0);
+        mbar_wait(&sh->p_empty[0], 0);
+    }
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 // ------------------------------------------------------------------ host side
 int tc_feature_kp(int d) { return ((6 * kernel_dim(d) + 6) + 15) / 16 * 16; }
+
+// Y (n x ldy, FP32) = K Omega^T on tensor cores; Om from launch_omega_bf16_tiled with
+// njc_alloc = (padded n) / 64 chunks per projection block.
+int launch_sketch_tc(krr_ctx* ctx, const unsigned char* FA, const unsigned char* FB, long long n, int d,
+                     const void* Om, int l, int njc_alloc, float* Y, int ldy) {
+    const int Kp = tc_feature_kp(d);
+    const uint32_t tileA = 128u * Kp * 2u, tileB1 = (uint32_t)SK_JC * Kp * 2u;
+    const size_t smem = tileA + (size_t)SK_NS * (tileB1 + SK_OMT) + 2 * 128 * SK_JC * 2 + 256;
+    KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)k_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    int* err;
+    KRR_RET(bufT(ctx, "tc_err", 1, &err));
+    KRR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+    const int nab = (l + SK_NB - 1) / SK_NB;
+    const int njc = (int)((n + SK_JC - 1) / SK_JC);
+    const int nrt = (int)((n + 127) / 128);
+    const int items = nrt * nab;
+    const int grid = std::min(items, ctx->num_sms);
+    k_sketch_tc<<<grid, SK_THREADS, smem, ctx->stream>>>(FA, FB, static_cast<const unsigned char*>(Om), Kp,
+                                                         (int)n, nab, njc, njc_alloc, items, Y, ldy, err);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
 
 int launch_tc_features(krr_ctx* ctx, const float* P, long long n, int d, int role,
                        unsigned char* out) {

@@ -139,6 +139,23 @@ def test_kmvm_tensor_core_rectangular_full_size(K):
     assert _relcols(Q[rows], ref).max() <= 1e-5
 
 
+def test_tensor_core_sketch_close_to_fp32_sketch(K):
+    # the build's BF16 tensor-core sketch against the FP32 sketch of the same Omega
+    p = synth.mixture(n=3000, k=200)
+    ctx = K(precision=1)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=9)
+    S_tc = ctx.anchors().cpu().numpy()
+    ctx0 = K(precision=0)
+    ctx0.build(_t(p.X), p.sigma, p.beta, p.k, seed=9)
+    S_32 = ctx0.anchors().cpu().numpy()
+    Kfull = O.kernel_matrix(p.X, p.X, p.sigma)
+    e_tc = np.linalg.norm(Kfull - O.Nystrom(p.X, S_tc, p.sigma, p.beta).ktilde(), 2)
+    e_32 = np.linalg.norm(Kfull - O.Nystrom(p.X, S_32, p.sigma, p.beta).ktilde(), 2)
+    assert e_tc <= 1.5 * e_32
+    # the leading pivots have large gaps and must agree
+    assert np.array_equal(S_tc[:20], S_32[:20])
+
+
 def test_solve_tensor_core_vs_dense(K):
     p = synth.small()
     ctx = K(precision=1)
