@@ -158,7 +158,10 @@ int krr_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sig
 int krr_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, float* OmT);
 
 /* Sketch Y = K(X, X) Omega^T of Algorithm 1 step 2: Y is n x l row-major
- * (Y[i*l + a]).  Omega is generated as krr_omega describes. */
+ * (Y[i*l + a]).  Omega is generated as krr_omega describes.  With opts.precision = 1
+ * (and d <= 16) the product runs on tensor cores with Omega and the kernel values
+ * rounded to BF16 (about 4e-3 relative error, which only steers the anchor choice);
+ * otherwise in FP32 tiles. */
 int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, int l,
                unsigned long long seed, float* Y);
 

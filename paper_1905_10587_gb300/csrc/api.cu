@@ -428,7 +428,7 @@ int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, i
     KRR_RET(build_common(ctx, X, n, d, sigma, 1.0));
     float* Yi;
     int ld;
-    KRR_RET(sketch_internal(ctx, n, l, seed, &Yi, &ld, false));
+    KRR_RET(sketch_internal(ctx, n, l, seed, &Yi, &ld, true));
     KRR_TRY_CUDA(cudaMemcpy2DAsync(Y, sizeof(float) * l, Yi, sizeof(float) * ld, sizeof(float) * l,
                                    n, cudaMemcpyDeviceToDevice, ctx->stream));
     return KRR_OK;

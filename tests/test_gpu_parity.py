@@ -152,8 +152,16 @@ def test_tensor_core_sketch_close_to_fp32_sketch(K):
     e_tc = np.linalg.norm(Kfull - O.Nystrom(p.X, S_tc, p.sigma, p.beta).ktilde(), 2)
     e_32 = np.linalg.norm(Kfull - O.Nystrom(p.X, S_32, p.sigma, p.beta).ktilde(), 2)
     assert e_tc <= 1.5 * e_32
-    # the leading pivots have large gaps and must agree
-    assert np.array_equal(S_tc[:20], S_32[:20])
+
+
+def test_tensor_core_sketch_vs_oracle(K):
+    # BF16 kernel values and Omega: each entry of Y within a few 1e-3 of the FP64 sketch
+    p = synth.small(n=1500)
+    l = 300
+    ctx = K(precision=1)
+    Y = ctx.sketch(_t(p.X), p.sigma, l, seed=11).cpu().numpy()
+    ref = O.sketch(p.X, p.sigma, O.omega(11, l, p.n))
+    assert _relcols(Y, ref).max() <= 1e-2
 
 
 def test_solve_tensor_core_vs_dense(K):
