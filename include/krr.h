@@ -226,6 +226,25 @@ int krr_kmvm_noalloc(const float* Xr, long long nr, const float* Xc, long long n
 int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alpha, int nrhs,
                 float* f);
 
+/* Derivative kernel product Q = (dK(Xr, Xc)/dlog sigma) V for one column: entries
+ * K_ij ||xr_i - xc_j||^2 / sigma^2, evaluated in FP32 tiles like krr_kmvm.  V (nc) and
+ * Q (nr) are FP32 device vectors.  Used by krr_grad. */
+int krr_kmvm_dsigma(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc, int d,
+                    double sigma, const float* V, float* Q);
+
+/* Gradient of the held-out mean squared error
+ *     L = ||K(Xval, X) alpha - yval||^2 / m,   alpha = (K + beta I)^{-1} y,
+ * with respect to log sigma, log beta and y, for the built (X, sigma, beta).  The
+ * paper has no gradient; this is the adjoint of its solve: with g = 2 (f - yval)/m
+ * and lambda = (K + beta I)^{-1} K(X, Xval) g (a second preconditioned solve),
+ *     dL/dy = lambda,   dL/dlog beta = -beta lambda . alpha,
+ *     dL/dlog sigma = g . (dK(Xval, X)/dlog sigma) alpha - lambda . (dK/dlog sigma) alpha,
+ * using dK_ij/dlog sigma = K_ij ||x_i - x_j||^2 / sigma^2 (a derivative kernel product).
+ * Y (n) and yval (m) are FP32 device vectors, Xval m x d; both solves run to tol.
+ * loss, dlogsigma, dlogbeta are host outputs; dy is an n-element FP64 device vector. */
+int krr_grad(krr_ctx* ctx, const float* Y, const float* Xval, long long m, const float* yval,
+             double tol, double* loss, double* dlogsigma, double* dlogbeta, double* dy);
+
 #ifdef __cplusplus
 }
 #endif

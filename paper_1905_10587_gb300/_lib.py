@@ -60,6 +60,8 @@ SIGNATURES = {
     "krr_precond_apply": (_i, [_vp, _vp, _i, _vp]),
     "krr_solve": (_i, [_vp, _vp, _vp, _i, _d, _vp, C.POINTER(KrrSolveInfo)]),
     "krr_predict": (_i, [_vp, _vp, _ll, _vp, _i, _vp]),
+    "krr_kmvm_dsigma": (_i, [_vp, _vp, _ll, _vp, _ll, _i, _d, _vp, _vp]),
+    "krr_grad": (_i, [_vp, _vp, _vp, _ll, _vp, _d, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), _vp]),
     "krr_kmvm_noalloc": (_i, [_vp, _ll, _vp, _ll, _i, _d, _d, _vp, _i, _vp, _vp,
                               C.POINTER(C.c_ulonglong)]),
 }

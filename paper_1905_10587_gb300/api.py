@@ -113,6 +113,16 @@ class KRR:
                                       Xr.shape[1], sigma, beta, _ptr(Vt), Vt.shape[0], _ptr(Q)))
         return _uncols(Q, vec)
 
+    def kmvm_dsigma(self, Xr, Xc, v, sigma: float) -> torch.Tensor:
+        """(dK(Xr, Xc)/dlog sigma) v for one column v."""
+        Xr = _cuda(Xr, torch.float32, "Xr")
+        Xc = _cuda(Xc, torch.float32, "Xc")
+        v = _cuda(v.reshape(-1), torch.float32, "v")
+        Q = torch.empty(Xr.shape[0], device=Xr.device, dtype=torch.float32)
+        self._check(self.lib.krr_kmvm_dsigma(self.h, _ptr(Xr), Xr.shape[0], _ptr(Xc), Xc.shape[0],
+                                             Xr.shape[1], sigma, _ptr(v), _ptr(Q)))
+        return Q
+
     def residual_hp(self, X, Y, A, sigma: float, beta: float, mode: str = "fp64") -> torch.Tensor:
         """Y - (K + beta I) A in FP64 ("fp64") or float-float ("ff"); A float64, Y float32."""
         X = _cuda(X, torch.float32, "X")
@@ -194,6 +204,21 @@ class KRR:
                    sweep_residual=[info.sweep_residual[i] for i in range(min(8, info.sweeps + 1))])
         return _uncols(A, vec), out
 
+    def grad(self, y, Xval, yval, tol: float = 1e-8):
+        """Held-out MSE and its gradient w.r.t. (log sigma, log beta, y) for the built problem.
+
+        Returns (loss, dL/dlog sigma, dL/dlog beta, dL/dy as an FP64 tensor)."""
+        if self._X is None:
+            raise KRRError(L.KRR_E_STATE, "grad before build")
+        y = _cuda(y.reshape(-1), torch.float32, "y")
+        Xv = _cuda(Xval, torch.float32, "Xval")
+        yv = _cuda(yval.reshape(-1), torch.float32, "yval")
+        dy = torch.empty(y.shape[0], device=y.device, dtype=torch.float64)
+        loss, ds, db = C.c_double(), C.c_double(), C.c_double()
+        self._check(self.lib.krr_grad(self.h, _ptr(y), _ptr(Xv), Xv.shape[0], _ptr(yv), tol,
+                                      C.byref(loss), C.byref(ds), C.byref(db), _ptr(dy)))
+        return loss.value, ds.value, db.value, dy
+
     def predict(self, Xtest, alpha) -> torch.Tensor:
         """f = K(Xtest, X) alpha (Eq. (1))."""
         Xt = _cuda(Xtest, torch.float32, "Xtest")
@@ -201,6 +226,41 @@ class KRR:
         f = torch.empty((At.shape[0], Xt.shape[0]), device=Xt.device, dtype=torch.float32)
         self._check(self.lib.krr_predict(self.h, _ptr(Xt), Xt.shape[0], _ptr(At), At.shape[0], _ptr(f)))
         return _uncols(f, vec)
+
+
+class ValidationLoss(torch.autograd.Function):
+    """Held-out MSE of Gaussian KRR as a differentiable function of (y, log sigma, log beta).
+
+    forward builds the preconditioner for (X, sigma, beta), solves, and runs the adjoint
+    solve of krr_grad; backward hands back the stored gradients.  X, Xval, yval, k, seed
+    and tol are constants (no gradient)."""
+
+    @staticmethod
+    def forward(fctx, y, log_sigma, log_beta, X, Xval, yval, k: int, seed: int = 0, tol: float = 1e-8,
+                precision: int = 0):
+        sigma = float(torch.exp(log_sigma.detach().double()))
+        beta = float(torch.exp(log_beta.detach().double()))
+        ctx = KRR(precision=precision)
+        ctx.build(X, sigma, beta, k, seed)
+        loss, ds, db, dy = ctx.grad(y.detach(), Xval, yval, tol)
+        ctx.close()
+        fctx.save_for_backward(dy)
+        fctx.ds, fctx.db, fctx.ydtype = ds, db, y.dtype
+        return torch.tensor(loss, dtype=torch.float64, device=y.device)
+
+    @staticmethod
+    def backward(fctx, gout):
+        (dy,) = fctx.saved_tensors
+        g = gout.to(torch.float64)
+        gy = (g * dy).to(fctx.ydtype)
+        gs = (g * fctx.ds).reshape(())
+        gb = (g * fctx.db).reshape(())
+        return gy, gs, gb, None, None, None, None, None, None, None
+
+
+def validation_loss(y, log_sigma, log_beta, X, Xval, yval, k, seed=0, tol=1e-8, precision=0):
+    """Differentiable held-out MSE (see ValidationLoss)."""
+    return ValidationLoss.apply(y, log_sigma, log_beta, X, Xval, yval, k, seed, tol, precision)
 
 
 def peak_probe(kind: int) -> float:

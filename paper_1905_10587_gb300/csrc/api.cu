@@ -87,6 +87,26 @@ int launch_cg_set_active(krr_ctx* ctx, const int* act_host, int nrhs);
 
 static const double LOG2E = 1.4426950408889634;
 
+// g = 2 (f - yv) / m and per-block partial sums of (f - yv)^2 (FP64)
+__global__ void k_val_grad(const float* __restrict__ f, const float* __restrict__ yv, long long m,
+                           float* __restrict__ g, double* __restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double r = (double)f[i] - (double)yv[i];
+        g[i] = (float)(2.0 * r / (double)m);
+        s += r * r;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
 static int check_points(krr_ctx* ctx, const void* X, long long n, int d) {
     if (!X) return fail(ctx, KRR_E_INVAL, "null point array");
     if (n < 1) return fail(ctx, KRR_E_INVAL, "n must be >= 1");
@@ -691,6 +711,91 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     if (info) *info = inf;
     if (status != KRR_OK) fail(ctx, status, "tolerance not reached");
     return status;
+}
+
+int krr_kmvm_dsigma(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc, int d,
+                    double sigma, const float* V, float* Q) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, Xr, nr, d));
+    KRR_RET(check_points(ctx, Xc, nc, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, 0.0, false));
+    if (!V || !Q) return fail(ctx, KRR_E_INVAL, "null V or Q");
+    const int ps = packed_stride(d);
+    const double s = LOG2E / (2.0 * sigma * sigma);
+    double* mu;
+    float *Pc, *Pr;
+    KRR_RET(bufT(ctx, "kmvm_mu", (size_t)d, &mu));
+    KRR_RET(bufT(ctx, "kmvm_Pc", (size_t)nc * ps, &Pc));
+    KRR_RET(bufT(ctx, "kmvm_Pr", (size_t)nr * ps, &Pr));
+    KRR_RET(launch_mean(ctx, Xc, nc, d, mu));
+    KRR_RET(launch_pack(ctx, Xc, nc, d, mu, s, Pc));
+    KRR_RET(launch_pack(ctx, Xr, nr, d, mu, s, Pr));
+    return launch_kmvm_dsigma(ctx, Pr, nr, Pc, nc, d, V, Q);
+}
+
+int krr_grad(krr_ctx* ctx, const float* Y, const float* Xval, long long m, const float* yval, double tol,
+             double* loss, double* dlogsigma, double* dlogbeta, double* dy) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!ctx->built) return fail(ctx, KRR_E_STATE, "krr_grad before krr_build_precond");
+    KRR_RET(check_points(ctx, Xval, m, ctx->d));
+    if (!Y || !yval || !loss || !dlogsigma || !dlogbeta || !dy)
+        return fail(ctx, KRR_E_INVAL, "null argument");
+    if (!(tol > 0.0) || !(tol < 1.0)) return fail(ctx, KRR_E_INVAL, "tol must be in (0, 1)");
+    const long long n = ctx->n;
+    const int d = ctx->d;
+    double *a64, *lam64, *tmp64, *sc;
+    float *a32, *f, *g, *b, *u1, *u2, *Pv;
+    KRR_RET(bufT(ctx, "gr_a64", (size_t)n, &a64));
+    KRR_RET(bufT(ctx, "gr_lam64", (size_t)n, &lam64));
+    KRR_RET(bufT(ctx, "gr_tmp64", (size_t)n, &tmp64));
+    KRR_RET(bufT(ctx, "gr_sc", 8, &sc));
+    KRR_RET(bufT(ctx, "gr_a32", (size_t)n, &a32));
+    KRR_RET(bufT(ctx, "gr_f", (size_t)m, &f));
+    KRR_RET(bufT(ctx, "gr_g", (size_t)m, &g));
+    KRR_RET(bufT(ctx, "gr_b", (size_t)n, &b));
+    KRR_RET(bufT(ctx, "gr_u1", (size_t)m, &u1));
+    KRR_RET(bufT(ctx, "gr_u2", (size_t)n, &u2));
+    KRR_RET(bufT(ctx, "gr_Pv", (size_t)m * ctx->ps, &Pv));
+    double* mu;
+    KRR_RET(bufT(ctx, "mu", (size_t)d, &mu));
+    const int nbv = (int)std::min<long long>(2LL * ctx->num_sms, ceil_div(m, 256));
+    double* vpart;
+    KRR_RET(bufT(ctx, "gr_vpart", (size_t)nbv, &vpart));
+
+    // alpha = (K + beta I)^{-1} y
+    int rc = krr_solve(ctx, ctx->X, Y, 1, tol, a64, nullptr);
+    if (rc != KRR_OK) return rc;
+    KRR_RET(launch_convert(ctx, a64, a32, n));
+    // f = K(Xval, X) alpha, g = 2 (f - yval) / m
+    KRR_RET(launch_pack(ctx, Xval, m, d, mu, ctx->s, Pv));
+    KRR_RET(launch_kmvm(ctx, Pv, m, ctx->P, n, d, 0.f, a32, 1, f));
+    k_val_grad<<<nbv, 256, 0, ctx->stream>>>(f, yval, m, g, vpart);
+    KRR_CHECK_LAUNCH();
+    // lambda = (K + beta I)^{-1} K(X, Xval) g  (the adjoint solve, same preconditioner)
+    KRR_RET(launch_kmvm(ctx, ctx->P, n, Pv, m, d, 0.f, g, 1, b));
+    rc = krr_solve(ctx, ctx->X, b, 1, tol, lam64, nullptr);
+    if (rc != KRR_OK) return rc;
+    KRR_TRY_CUDA(cudaMemcpyAsync(dy, lam64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    // dL/dlog beta = -beta lambda . alpha
+    KRR_RET(launch_dot64(ctx, lam64, a64, n, 1, sc + 0));
+    // dL/dlog sigma = g . dK(Xval, X) alpha - lambda . dK(X, X) alpha
+    KRR_RET(launch_kmvm_dsigma(ctx, Pv, m, ctx->P, n, d, a32, u1));
+    KRR_RET(launch_dot(ctx, g, u1, m, 1, sc + 1));
+    KRR_RET(launch_kmvm_dsigma(ctx, ctx->P, n, ctx->P, n, d, a32, u2));
+    KRR_RET(launch_convert_up(ctx, u2, tmp64, n));
+    KRR_RET(launch_dot64(ctx, lam64, tmp64, n, 1, sc + 2));
+    double h[3];
+    std::vector<double> vp(nbv);
+    KRR_TRY_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    KRR_TRY_CUDA(cudaMemcpyAsync(vp.data(), vpart, sizeof(double) * nbv, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    double ssq = 0.0;
+    for (double v : vp) ssq += v;
+    *loss = ssq / (double)m;
+    *dlogbeta = -ctx->beta * h[0];
+    *dlogsigma = h[1] - h[2];
+    return KRR_OK;
 }
 
 int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alpha, int nrhs,

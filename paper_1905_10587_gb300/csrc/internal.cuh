@@ -176,6 +176,9 @@ int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double 
 
 int launch_kmvm_reduce(krr_ctx* ctx, const float* part, int splits, int nr, int nrhs, const float* V,
                        int ldv, float beta, float* Q, int ldq);
+// Q = (dK/dlog sigma)(Pr, Pc) v, one column
+int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc,
+                       int d, const float* V, float* Q);
 
 // tc_kmvm.cu: BF16x3 tcgen05 product (d <= 16).  Features: role 0 rows, 1 columns.
 int tc_feature_kp(int d);

@@ -341,6 +341,107 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
     return KRR_OK;
 }
 
+// ------------------------------------------------------------------ derivative product
+// Q_i = sum_j (dK/dlog sigma)_ij v_j with (dK/dlog sigma)_ij = K_ij ||x_i - x_j||^2 / sigma^2.
+// In the packed coordinates t_ij = a_i + a_j + 2 xh_i . xh_j = -s ||x_i - x_j||^2 with
+// s = log2(e) / (2 sigma^2), so the entry is -2 ln2 t_ij 2^t_ij: one extra multiply per pair.
+template <int D, int R>
+__global__ void __launch_bounds__(KM_THREADS, 4)
+k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
+              const float* __restrict__ V, int tiles_per_split, float* __restrict__ part) {
+    constexpr int PS = (D + 1 + 3) / 4 * 4;
+    constexpr int PS4 = PS / 4;
+    __shared__ float4 sP[KM_BN * PS4];
+    __shared__ float sV[KM_BN];
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * (KM_THREADS * R);
+    float xi[R][D], ai[R], acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = row0 + r * KM_THREADS + tid;
+        const bool ok = i < nr;
+#pragma unroll
+        for (int c = 0; c < D; ++c) xi[r][c] = ok ? 2.f * Pr[i * PS + c] : 0.f;
+        ai[r] = ok ? Pr[i * PS + D] : 0.f;
+        acc[r] = 0.f;
+    }
+    const int ntiles = (nc + KM_BN - 1) / KM_BN;
+    const int t0 = blockIdx.y * tiles_per_split;
+    const int t1 = min(t0 + tiles_per_split, ntiles);
+    const float4* Pc4 = reinterpret_cast<const float4*>(Pc);
+    for (int t = t0; t < t1; ++t) {
+        const int c0 = t * KM_BN;
+        for (int e = tid; e < KM_BN * PS4; e += KM_THREADS) {
+            const int j = e / PS4;
+            sP[e] = (c0 + j < nc) ? Pc4[(size_t)(c0 + j) * PS4 + (e - j * PS4)]
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = tid; e < KM_BN; e += KM_THREADS) sV[e] = (c0 + e < nc) ? V[c0 + e] : 0.f;
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < KM_BN; ++j) {
+            float xj[PS];
+#pragma unroll
+            for (int w = 0; w < PS4; ++w) {
+                const float4 v = sP[j * PS4 + w];
+                xj[4 * w + 0] = v.x;
+                xj[4 * w + 1] = v.y;
+                xj[4 * w + 2] = v.z;
+                xj[4 * w + 3] = v.w;
+            }
+            const float vj = sV[j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float tt = ai[r] + xj[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) tt = fmaf(xi[r][c], xj[c], tt);
+                acc[r] = fmaf(tt * ex2f(tt), vj, acc[r]);
+            }
+        }
+        __syncthreads();
+    }
+    const float scale = -2.f * 0.6931471805599453f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = row0 + r * KM_THREADS + tid;
+        if (i < nr) part[(size_t)blockIdx.y * nr + i] = scale * acc[r];
+    }
+}
+
+typedef void (*dsig_fn)(const float*, int, const float*, int, const float*, int, float*);
+
+static dsig_fn dsig_pick(int dk) {
+    switch (dk) {
+#define KRR_D(v) \
+    case v: return &k_kmvm_dsigma<v, (v > 32 ? 1 : v > 16 ? 2 : 4)>;
+        KRR_D(1) KRR_D(2) KRR_D(3) KRR_D(4) KRR_D(5) KRR_D(6) KRR_D(7) KRR_D(8)
+        KRR_D(9) KRR_D(10) KRR_D(11) KRR_D(12) KRR_D(13) KRR_D(14) KRR_D(15) KRR_D(16)
+        KRR_D(24) KRR_D(32) KRR_D(48) KRR_D(64)
+#undef KRR_D
+    }
+    return nullptr;
+}
+
+// Q = (dK(Pr, Pc)/dlog sigma) v for one column v (nc), Q (nr).
+int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc,
+                       int d, const float* V, float* Q) {
+    const int dk = kernel_dim(d);
+    dsig_fn fn = dsig_pick(dk);
+    if (!fn) return fail(ctx, KRR_E_INVAL, "dsigma: unsupported dimension");
+    const int R = dk > 32 ? 1 : dk > 16 ? 2 : 4;
+    const int nblk = (int)ceil_div(nr, KM_THREADS * R);
+    const int ntiles = (int)ceil_div(nc, KM_BN);
+    const int slots = ctx->num_sms * occupancy(ctx, (const void*)fn, KM_THREADS);
+    int splits = choose_splits(nblk, ntiles, slots);
+    const int tps = (ntiles + splits - 1) / splits;
+    splits = (ntiles + tps - 1) / tps;
+    float* part;
+    KRR_RET(bufT(ctx, "dsig_part", (size_t)splits * nr, &part));
+    fn<<<dim3(nblk, splits), KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, V, tps, part);
+    KRR_CHECK_LAUNCH();
+    return launch_kmvm_reduce(ctx, part, splits, (int)nr, 1, V, (int)nc, 0.f, Q, (int)nr);
+}
+
 // ------------------------------------------------------------------ product into given scratch
 // The FP32 product K(Xr, Xc) V + beta V with every temporary (mean, packed points,
 // split-K partial sums) carved from one caller-provided device buffer: no device
