@@ -240,6 +240,9 @@ int krr_kmvm_dsigma(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc
  *     dL/dy = lambda,   dL/dlog beta = -beta lambda . alpha,
  *     dL/dlog sigma = g . (dK(Xval, X)/dlog sigma) alpha - lambda . (dK/dlog sigma) alpha,
  * using dK_ij/dlog sigma = K_ij ||x_i - x_j||^2 / sigma^2 (a derivative kernel product).
+ * The four kernel products (f, the adjoint right-hand side and both derivative
+ * products) are evaluated in float-float, since the sigma term is a difference of two
+ * products that cancel.  Needs d <= 16.
  * Y (n) and yval (m) are FP32 device vectors, Xval m x d; both solves run to tol.
  * loss, dlogsigma, dlogbeta are host outputs; dy is an n-element FP64 device vector. */
 int krr_grad(krr_ctx* ctx, const float* Y, const float* Xval, long long m, const float* yval,

@@ -87,6 +87,26 @@ int launch_cg_set_active(krr_ctx* ctx, const int* act_host, int nrhs);
 
 static const double LOG2E = 1.4426950408889634;
 
+// g = 2 (f - yv) / m and per-block partial sums of (f - yv)^2, all FP64
+__global__ void k_val_grad64(const double* __restrict__ f, const float* __restrict__ yv, long long m,
+                             double* __restrict__ g, double* __restrict__ part) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double r = f[i] - (double)yv[i];
+        g[i] = 2.0 * r / (double)m;
+        s += r * r;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
 // g = 2 (f - yv) / m and per-block partial sums of (f - yv)^2 (FP64)
 __global__ void k_val_grad(const float* __restrict__ f, const float* __restrict__ yv, long long m,
                            float* __restrict__ g, double* __restrict__ part) {
@@ -741,49 +761,47 @@ int krr_grad(krr_ctx* ctx, const float* Y, const float* Xval, long long m, const
     if (!Y || !yval || !loss || !dlogsigma || !dlogbeta || !dy)
         return fail(ctx, KRR_E_INVAL, "null argument");
     if (!(tol > 0.0) || !(tol < 1.0)) return fail(ctx, KRR_E_INVAL, "tol must be in (0, 1)");
+    if (ctx->d > 16) return fail(ctx, KRR_E_INVAL, "krr_grad needs d <= 16");
     const long long n = ctx->n;
     const int d = ctx->d;
-    double *a64, *lam64, *tmp64, *sc;
-    float *a32, *f, *g, *b, *u1, *u2, *Pv;
+    double *a64, *lam64, *f64, *g64, *b64, *u1, *u2, *sc;
+    float* b32;
     KRR_RET(bufT(ctx, "gr_a64", (size_t)n, &a64));
     KRR_RET(bufT(ctx, "gr_lam64", (size_t)n, &lam64));
-    KRR_RET(bufT(ctx, "gr_tmp64", (size_t)n, &tmp64));
-    KRR_RET(bufT(ctx, "gr_sc", 8, &sc));
-    KRR_RET(bufT(ctx, "gr_a32", (size_t)n, &a32));
-    KRR_RET(bufT(ctx, "gr_f", (size_t)m, &f));
-    KRR_RET(bufT(ctx, "gr_g", (size_t)m, &g));
-    KRR_RET(bufT(ctx, "gr_b", (size_t)n, &b));
+    KRR_RET(bufT(ctx, "gr_f64", (size_t)m, &f64));
+    KRR_RET(bufT(ctx, "gr_g64", (size_t)m, &g64));
+    KRR_RET(bufT(ctx, "gr_b64", (size_t)n, &b64));
     KRR_RET(bufT(ctx, "gr_u1", (size_t)m, &u1));
     KRR_RET(bufT(ctx, "gr_u2", (size_t)n, &u2));
-    KRR_RET(bufT(ctx, "gr_Pv", (size_t)m * ctx->ps, &Pv));
-    double* mu;
-    KRR_RET(bufT(ctx, "mu", (size_t)d, &mu));
+    KRR_RET(bufT(ctx, "gr_sc", 8, &sc));
+    KRR_RET(bufT(ctx, "gr_b32", (size_t)n, &b32));
     const int nbv = (int)std::min<long long>(2LL * ctx->num_sms, ceil_div(m, 256));
     double* vpart;
     KRR_RET(bufT(ctx, "gr_vpart", (size_t)nbv, &vpart));
 
+    // Every kernel product here is evaluated in float-float: the sigma gradient is a
+    // difference of two products that cancel, and finite differences of the loss need it
+    // far below FP32 noise.
     // alpha = (K + beta I)^{-1} y
     int rc = krr_solve(ctx, ctx->X, Y, 1, tol, a64, nullptr);
     if (rc != KRR_OK) return rc;
-    KRR_RET(launch_convert(ctx, a64, a32, n));
-    // f = K(Xval, X) alpha, g = 2 (f - yval) / m
-    KRR_RET(launch_pack(ctx, Xval, m, d, mu, ctx->s, Pv));
-    KRR_RET(launch_kmvm(ctx, Pv, m, ctx->P, n, d, 0.f, a32, 1, f));
-    k_val_grad<<<nbv, 256, 0, ctx->stream>>>(f, yval, m, g, vpart);
+    // f = K(Xval, X) alpha;  g = 2 (f - yval) / m
+    KRR_RET(launch_rect_ff(ctx, Xval, m, ctx->X, n, d, ctx->sigma, a64, 0, f64));
+    k_val_grad64<<<nbv, 256, 0, ctx->stream>>>(f64, yval, m, g64, vpart);
     KRR_CHECK_LAUNCH();
-    // lambda = (K + beta I)^{-1} K(X, Xval) g  (the adjoint solve, same preconditioner)
-    KRR_RET(launch_kmvm(ctx, ctx->P, n, Pv, m, d, 0.f, g, 1, b));
-    rc = krr_solve(ctx, ctx->X, b, 1, tol, lam64, nullptr);
+    // lambda = (K + beta I)^{-1} K(X, Xval) g  (adjoint solve, same preconditioner)
+    KRR_RET(launch_rect_ff(ctx, ctx->X, n, Xval, m, d, ctx->sigma, g64, 0, b64));
+    KRR_RET(launch_convert(ctx, b64, b32, n));
+    rc = krr_solve(ctx, ctx->X, b32, 1, tol, lam64, nullptr);
     if (rc != KRR_OK) return rc;
     KRR_TRY_CUDA(cudaMemcpyAsync(dy, lam64, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     // dL/dlog beta = -beta lambda . alpha
     KRR_RET(launch_dot64(ctx, lam64, a64, n, 1, sc + 0));
     // dL/dlog sigma = g . dK(Xval, X) alpha - lambda . dK(X, X) alpha
-    KRR_RET(launch_kmvm_dsigma(ctx, Pv, m, ctx->P, n, d, a32, u1));
-    KRR_RET(launch_dot(ctx, g, u1, m, 1, sc + 1));
-    KRR_RET(launch_kmvm_dsigma(ctx, ctx->P, n, ctx->P, n, d, a32, u2));
-    KRR_RET(launch_convert_up(ctx, u2, tmp64, n));
-    KRR_RET(launch_dot64(ctx, lam64, tmp64, n, 1, sc + 2));
+    KRR_RET(launch_rect_ff(ctx, Xval, m, ctx->X, n, d, ctx->sigma, a64, 1, u1));
+    KRR_RET(launch_dot64(ctx, g64, u1, m, 1, sc + 1));
+    KRR_RET(launch_rect_ff(ctx, ctx->X, n, ctx->X, n, d, ctx->sigma, a64, 1, u2));
+    KRR_RET(launch_dot64(ctx, lam64, u2, n, 1, sc + 2));
     double h[3];
     std::vector<double> vp(nbv);
     KRR_TRY_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));

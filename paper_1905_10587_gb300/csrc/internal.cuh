@@ -195,6 +195,10 @@ int launch_omega_bf16_tiled(krr_ctx* ctx, unsigned long long seed, int l, long l
 int launch_residual_ff(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);
 
+// out = K(Xr, Xc) a (mode 0) or (dK/dlog sigma) a (mode 1) in float-float (d <= 16)
+int launch_rect_ff(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc, int d,
+                   double sigma, const double* a, int mode, double* out);
+
 // sketch.cu
 int launch_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, int ld, float* OmT);
 // Out[i*ldo + a] = sum_j K(Pr_i, Pc_j) V[j*ldv + a], a < ncol (FP32 SIMT contraction)

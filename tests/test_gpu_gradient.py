@@ -96,7 +96,7 @@ def test_autograd_function_matches_grad():
     ctx = KRR()
     ctx.build(X, p.sigma, p.beta, p.k, seed=3)
     loss, ds, db, dy = ctx.grad(y.detach(), Xv, yv, tol=1e-9)
-    assert float(L) == pytest.approx(loss, rel=1e-9)
+    assert float(L.detach()) == pytest.approx(loss, rel=1e-9)
     assert float(ls.grad) == pytest.approx(ds, rel=1e-6)
     assert float(lb.grad) == pytest.approx(db, rel=1e-6)
     np.testing.assert_allclose(y.grad.double().cpu().numpy(), dy.cpu().numpy(), rtol=1e-5, atol=1e-12)
