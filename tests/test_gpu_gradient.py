@@ -99,4 +99,6 @@ def test_autograd_function_matches_grad():
     assert float(L.detach()) == pytest.approx(loss, rel=1e-9)
     assert float(ls.grad) == pytest.approx(ds, rel=1e-6)
     assert float(lb.grad) == pytest.approx(db, rel=1e-6)
-    np.testing.assert_allclose(y.grad.double().cpu().numpy(), dy.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    # two separate builds (sigma = exp(log sigma) differs in the last bit), each solved to 1e-9
+    gy, ref = y.grad.double().cpu().numpy(), dy.cpu().numpy()
+    assert np.linalg.norm(gy - ref) / np.linalg.norm(ref) <= 1e-6
