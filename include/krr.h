@@ -248,6 +248,30 @@ int krr_kmvm_dsigma(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc
 int krr_grad(krr_ctx* ctx, const float* Y, const float* Xval, long long m, const float* yval,
              double tol, double* loss, double* dlogsigma, double* dlogbeta, double* dy);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves (many independent problems of uneven size; the paper solves one
+ * problem at a time).  Each problem is built (Algorithms 1 and 3, anchor seed
+ * seed + index) and solved (Algorithm 5) to tol with nrhs right-hand sides, as
+ * krr_build_precond + krr_solve would.  W worker threads (workers <= 0: 8), each
+ * with its own CUDA stream and context, take problems largest n^2 first, so several
+ * problems' kernels overlap on the GPU.  All problem arrays are device pointers;
+ * probs, infos and statuses are host arrays of nprob entries (infos, statuses may be
+ * NULL).  The call returns when every problem is done: KRR_OK, or the first
+ * non-OK status of a problem (KRR_E_NOCONV when some problem stopped early).
+ * ------------------------------------------------------------------------- */
+typedef struct krr_problem {
+    const float* X;     /* n x d, row-major                       */
+    long long n;
+    int d;
+    const float* Y;     /* n x nrhs, RHS-major                    */
+    double sigma, beta;
+    int k;
+    double* alpha;      /* n x nrhs FP64 output, RHS-major        */
+} krr_problem;
+
+int krr_batch_solve(const krr_problem* probs, int nprob, int nrhs, double tol, unsigned long long seed,
+                    const krr_opts* opts, int workers, krr_solve_info* infos, int* statuses);
+
 #ifdef __cplusplus
 }
 #endif

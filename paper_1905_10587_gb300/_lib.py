@@ -37,6 +37,11 @@ class KrrSolveInfo(C.Structure):
 
 _vp, _i, _ll, _d, _ull = C.c_void_p, C.c_int, C.c_longlong, C.c_double, C.c_ulonglong
 
+
+class KrrProblem(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("n", C.c_longlong), ("d", C.c_int), ("Y", C.c_void_p),
+                ("sigma", C.c_double), ("beta", C.c_double), ("k", C.c_int), ("alpha", C.c_void_p)]
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "krr_default_opts": (_i, [C.POINTER(KrrOpts)]),
@@ -60,6 +65,8 @@ SIGNATURES = {
     "krr_precond_apply": (_i, [_vp, _vp, _i, _vp]),
     "krr_solve": (_i, [_vp, _vp, _vp, _i, _d, _vp, C.POINTER(KrrSolveInfo)]),
     "krr_predict": (_i, [_vp, _vp, _ll, _vp, _i, _vp]),
+    "krr_batch_solve": (_i, [C.POINTER(KrrProblem), _i, _i, _d, _ull, C.POINTER(KrrOpts), _i,
+                             C.POINTER(KrrSolveInfo), C.POINTER(_i)]),
     "krr_kmvm_dsigma": (_i, [_vp, _vp, _ll, _vp, _ll, _i, _d, _vp, _vp]),
     "krr_grad": (_i, [_vp, _vp, _vp, _ll, _vp, _d, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), _vp]),
     "krr_kmvm_noalloc": (_i, [_vp, _ll, _vp, _ll, _i, _d, _d, _vp, _i, _vp, _vp,

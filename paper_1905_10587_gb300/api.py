@@ -273,6 +273,44 @@ def peak_probe(kind: int) -> float:
     return v.value
 
 
+def batch_solve(problems, tol: float = 1e-6, seed: int = 0, workers: int = 8, **opts):
+    """Solve independent problems concurrently (krr_batch_solve).
+
+    problems: list of (X (n, d), Y (n, nrhs) or (n,), sigma, beta, k) CUDA tensors/values,
+    all with the same number of right-hand sides.  Returns (list of FP64 alpha tensors,
+    list of info dicts, list of status codes)."""
+    lib = L.load()
+    o = L.KrrOpts()
+    lib.krr_default_opts(C.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, v)
+    arr = (L.KrrProblem * len(problems))()
+    keep, alphas, nrhs = [], [], None
+    for i, (X, Y, sigma, beta, k) in enumerate(problems):
+        X = _cuda(X, torch.float32, "X")
+        Yt, vec = _cols(Y, torch.float32, "Y")
+        if nrhs is None:
+            nrhs = Yt.shape[0]
+        elif nrhs != Yt.shape[0]:
+            raise ValueError("all problems need the same number of right-hand sides")
+        A = torch.empty(Yt.shape, device=Yt.device, dtype=torch.float64)
+        keep += [X, Yt]
+        alphas.append((A, vec))
+        arr[i] = L.KrrProblem(X.data_ptr(), X.shape[0], X.shape[1], Yt.data_ptr(), sigma, beta, k,
+                              A.data_ptr())
+    infos = (L.KrrSolveInfo * len(problems))()
+    stats = (C.c_int * len(problems))()
+    torch.cuda.synchronize()
+    rc = lib.krr_batch_solve(arr, len(problems), nrhs, tol, seed, C.byref(o), workers, infos, stats)
+    if rc not in (0, L.KRR_E_NOCONV):
+        raise KRRError(rc, "batch solve failed")
+    out = [_uncols(A, vec) for A, vec in alphas]
+    info = [dict(status=f.status, iters=f.iters, sweeps=f.sweeps, k_eff=f.k_eff,
+                 rel_residual=[f.rel_residual[j] for j in range(nrhs)], solve_ms=f.solve_ms,
+                 build_ms=f.build_ms) for f in infos]
+    return out, info, list(stats)
+
+
 def tc_selftest(variant: int = 0):
     """(mismatches, max_err) of the tcgen05 known-answer test."""
     lib = L.load()

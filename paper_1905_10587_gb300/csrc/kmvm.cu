@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 
 namespace krr {
 
@@ -270,13 +271,19 @@ static kmvm_fn pick(int dk, int nrhs, int* R) {
 }
 
 static int occupancy(krr_ctx* ctx, const void* fn, int threads) {
+    (void)ctx;
+    static std::mutex mu;   // contexts may run on several host threads (batched solves)
     static std::map<const void*, int> cache;
-    auto it = cache.find(fn);
-    if (it != cache.end()) return it->second;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(fn);
+        if (it != cache.end()) return it->second;
+    }
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess ||
         occ < 1)
         occ = 1;
+    std::lock_guard<std::mutex> lock(mu);
     cache[fn] = occ;
     return occ;
 }
