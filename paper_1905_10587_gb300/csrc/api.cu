@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace krr {
@@ -15,6 +16,19 @@ namespace krr {
 int fail(krr_ctx* ctx, int code, const std::string& msg) {
     if (ctx) ctx->err = msg;
     return code;
+}
+
+int allow_max_dynamic_smem(krr_ctx* ctx, const void* fn) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(fn)) return KRR_OK;
+    int dev = 0, optin = 0;
+    KRR_TRY_CUDA(cudaGetDevice(&dev));
+    KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    KRR_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    done[fn] = 1;
+    return KRR_OK;
 }
 
 const char* const kPhaseNames[PH_COUNT] = {"kmvm", "sketch", "omega", "qrcp", "fgemm", "gram",

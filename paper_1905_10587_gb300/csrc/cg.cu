@@ -325,8 +325,7 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
         KRR_CHECK_LAUNCH();
         const size_t smem = sizeof(float4) * nq * (ldF / 4);
         if (smem > 48 * 1024) {
-            KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)gn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem));
+            KRR_RET(allow_max_dynamic_smem(ctx, (const void*)gn));
         }
         gn<<<nb, VT, smem, ctx->stream>>>(ctx->F, n, k, ldF, v, Rq, n, inv_beta, Zq,
                                           rz_part ? rz_part + (size_t)q0 * nb : nullptr);

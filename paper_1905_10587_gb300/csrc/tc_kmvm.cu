@@ -648,8 +648,7 @@ int launch_sketch_tc(krr_ctx* ctx, const unsigned char* FA, const unsigned char*
     const int Kp = tc_feature_kp(d);
     const uint32_t tileA = 128u * Kp * 2u, tileB1 = (uint32_t)SK_JC * Kp * 2u;
     const size_t smem = tileA + (size_t)SK_NS * (tileB1 + SK_OMT) + 2 * 128 * SK_JC * 2 + 256;
-    KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)k_sketch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    KRR_RET(allow_max_dynamic_smem(ctx, (const void*)k_sketch_tc));
     int* err;
     KRR_RET(bufT(ctx, "tc_err", 1, &err));
     KRR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
@@ -707,8 +706,7 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         const uint32_t tileA = 128u * Kp * 2u;
         const size_t smem = (2 + TC_NS) * (size_t)tileA + (size_t)TC_NS * chunk * TC_BN * 4 + 256;
         const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
-        KRR_TRY_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem_launch));
+        KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
         const int nrb = (int)ceil_div(nr, TC_ROWS);
         const int ntiles = ncp / TC_BN;
         int splits = choose_splits_public(nrb, ntiles, ctx->num_sms);
