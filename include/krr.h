@@ -67,7 +67,10 @@ typedef struct krr_opts {
                              split GEMM (d <= 16; larger d uses the FP32 tiles)          */
     int    residual;      /* refinement residual: 0 float-float on the FP32 pipe
                              (default), 1 FP64 pipe                                      */
-    int    reserved[6];
+    double pivot_tol;     /* the anchor set ends at the first anchor whose Cholesky pivot
+                             in K_SS (its variance given the earlier anchors; K_SS has a
+                             unit diagonal) is <= pivot_tol (default 1e-6)              */
+    int    reserved[4];
 } krr_opts;
 
 /* Per-solve report (host struct). */

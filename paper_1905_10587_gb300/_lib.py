@@ -25,7 +25,8 @@ KRR_E_STATE, KRR_E_NOMEM, KRR_E_NONFINITE = 5, 6, 7
 class KrrOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("refine_max", C.c_int), ("oversample", C.c_int),
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
-                ("precision", C.c_int), ("residual", C.c_int), ("reserved", C.c_int * 6)]
+                ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
+                ("reserved", C.c_int * 4)]
 
 
 class KrrSolveInfo(C.Structure):

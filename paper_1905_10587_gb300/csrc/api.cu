@@ -179,22 +179,28 @@ static int build_from_anchors(krr_ctx* ctx, const int* S_dev, int k_eff) {
         KRR_RET(launch_gather_pack(ctx, ctx->P, ps, ctx->X, d, ctx->S, k_eff, ctx->PS, ctx->XS));
     }
 
-    // L1 L1^T = K_SS (FP64); a tiny diagonal shift is added only if the factorisation fails
+    // L1 L1^T = K_SS (FP64), anchors in pivot order.  K_SS has a unit diagonal, so the
+    // Cholesky pivot of anchor j is its conditional variance given the anchors before it;
+    // where it falls below opts.pivot_tol the anchor adds nothing FP32 arithmetic can
+    // resolve and only inflates L1^{-1}, so the anchor set ends there (the columns before
+    // the failing one are final; the factor is recomputed for the kept prefix).
     double *L1, *L1inv;
     KRR_RET(bufT(ctx, "L1", (size_t)k_eff * k_eff, &L1));
     KRR_RET(bufT(ctx, "L1inv", (size_t)k_eff * k_eff, &L1inv));
     int info = 0;
-    double shift = 0.0;
     {
         Phase ph_chol(ctx, PH_CHOL);
-        for (int attempt = 0; attempt < 4; ++attempt) {
-            KRR_RET(launch_kss(ctx, ctx->XS, k_eff, d, ctx->sigma, L1));
-            if (shift > 0.0) KRR_RET(launch_add_diag(ctx, L1, k_eff, shift));
-            KRR_RET(launch_potrf(ctx, L1, k_eff, &info));
-            if (info == 0) break;
-            shift = shift == 0.0 ? 1e-12 * k_eff : shift * 1e3;
+        KRR_RET(launch_kss(ctx, ctx->XS, k_eff, d, ctx->sigma, L1));
+        KRR_RET(launch_potrf(ctx, L1, k_eff, &info, ctx->opts.pivot_tol));
+        if (info != 0) {
+            const int keep = info - 1;
+            if (keep < 1) return fail(ctx, KRR_E_NONFINITE, "first anchor pivot is not positive");
+            k_eff = keep;
+            ctx->k_eff = keep;
+            KRR_RET(launch_kss(ctx, ctx->XS, k_eff, d, ctx->sigma, L1));   // prefix of the same S
+            KRR_RET(launch_potrf(ctx, L1, k_eff, &info, 0.0));
+            if (info != 0) return fail(ctx, KRR_E_NOTSPD, "Cholesky of K_SS failed");
         }
-        if (info != 0) return fail(ctx, KRR_E_NOTSPD, "Cholesky of K_SS failed");
         KRR_RET(launch_set_identity(ctx, L1inv, k_eff));
         KRR_RET(launch_trsm_lower(ctx, L1, L1inv, k_eff));
     }
@@ -280,6 +286,7 @@ int krr_default_opts(krr_opts* o) {
     o->check_every = 1;
     o->inner_tol = 1e-2;
     o->anchor_rtol = 1e-5;
+    o->pivot_tol = 1e-6;
     o->precision = 0;
     return KRR_OK;
 }
@@ -294,7 +301,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.check_every < 1 || !(ctx->opts.inner_tol > 0.0) || ctx->opts.inner_tol >= 1.0 ||
         ctx->opts.residual < 0 || ctx->opts.residual > 1 || ctx->opts.precision < 0 ||
         ctx->opts.precision > 1 ||
-        !(ctx->opts.anchor_rtol >= 0.0)) {
+        !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
     }

@@ -35,14 +35,14 @@ int launch_kss(krr_ctx* ctx, const float* XS, int k, int d, double sigma, double
 
 // ---- unblocked Cholesky of the nb x nb diagonal block at (j0, j0); one CTA of NB x NB threads.
 __global__ void __launch_bounds__(NB * NB)
-k_potf2(double* __restrict__ A, int k, int j0, int nb, int* __restrict__ info) {
+k_potf2(double* __restrict__ A, int k, int j0, int nb, double tau, int* __restrict__ info) {
     __shared__ double s[NB][NB + 1];
     const int r = threadIdx.y, c = threadIdx.x;
     s[r][c] = (r < nb && c < nb) ? A[(size_t)(j0 + r) * k + j0 + c] : 0.0;
     __syncthreads();
     for (int m = 0; m < nb; ++m) {
         const double piv = s[m][m];
-        const bool bad = !(piv > 0.0) || !isfinite(piv);
+        const bool bad = !(piv > tau) || !isfinite(piv);
         if (bad) {
             if (r == 0 && c == 0) atomicCAS(info, 0, j0 + m + 1);
             return;   // uniform: every thread sees the same s[m][m]
@@ -121,13 +121,13 @@ __global__ void k_zero_upper(double* A, int k) {
     if (c > r) A[e] = 0.0;
 }
 
-int launch_potrf(krr_ctx* ctx, double* A, int k, int* info_host) {
+int launch_potrf(krr_ctx* ctx, double* A, int k, int* info_host, double tau) {
     int* info;
     KRR_RET(bufT(ctx, "potrf_info", 1, &info));
     KRR_TRY_CUDA(cudaMemsetAsync(info, 0, sizeof(int), ctx->stream));
     for (int j0 = 0; j0 < k; j0 += NB) {
         const int nb = std::min(NB, k - j0);
-        k_potf2<<<1, dim3(NB, NB), 0, ctx->stream>>>(A, k, j0, nb, info);
+        k_potf2<<<1, dim3(NB, NB), 0, ctx->stream>>>(A, k, j0, nb, tau, info);
         KRR_CHECK_LAUNCH();
         const int rest = k - j0 - nb;
         if (rest <= 0) break;

@@ -218,8 +218,9 @@ int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int*
 // dense64.cu
 int launch_kss(krr_ctx* ctx, const float* XS, int k, int d, double sigma, double* A);
 // In-place lower Cholesky of the k x k row-major A (upper part ignored).  Sets *info
-// (host) to 0 or to 1 + the failing column.
-int launch_potrf(krr_ctx* ctx, double* A, int k, int* info);
+// (host) to 0 or to 1 + the first column whose pivot is <= tau (or not finite); the
+// columns before it are final.
+int launch_potrf(krr_ctx* ctx, double* A, int k, int* info, double tau = 0.0);
 // Solve L X = B in place (B k x k row-major), L lower k x k row-major.
 int launch_trsm_lower(krr_ctx* ctx, const double* L, double* B, int k);
 int launch_transpose64(krr_ctx* ctx, const double* A, double* At, int k);
