@@ -131,7 +131,10 @@ int krr_peak_probe(int kind, double* ops_per_s, void* stream);
  * Q = K(Xr, Xc) V + beta * V[0:nr]   (Q: nr x nrhs, V: nc x nrhs, RHS-major).
  * K(Xr, Xc)_ij = exp(-||xr_i - xc_j||^2 / (2 sigma^2)), evaluated in FP32 tiles
  * from the expansion ||x||^2 + ||y||^2 - 2 x.y after centring both sets on the
- * mean of Xc; K is never stored.  beta must be 0 unless nr == nc (square
+ * mean of Xc; K is never stored.  Each thread sums one 128-column tile in
+ * FP32 and folds the tile sums in FP64 (smooth kernels with mixed-sign V cancel
+ * heavily, and an FP32 running sum over 10^5 columns loses about beta of the
+ * result).  beta must be 0 unless nr == nc (square
  * product with the ridge term).  Xr may equal Xc.
  * ------------------------------------------------------------------------- */
 int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc,
@@ -209,7 +212,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
  * exists for callers that may not allocate device memory, such as an
  * application that owns all GPU memory through its own pool, or code running
  * where a cudaMalloc is not allowed.  It computes the same product as krr_kmvm
- * (FP32 tiles; no context needed), taking all temporaries from one fixed device
+ * (no context needed), taking all temporaries from one fixed device
  * array of KRR_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps
  * until the process exits.  The first call on a device looks up that array's
  * device address, so make that first call before any stream capture.  Calls

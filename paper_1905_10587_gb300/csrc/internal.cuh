@@ -179,7 +179,7 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
 int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);
 
-int launch_kmvm_reduce(krr_ctx* ctx, const float* part, int splits, int nr, int nrhs, const float* V,
+int launch_kmvm_reduce(krr_ctx* ctx, const double* part, int splits, int nr, int nrhs, const float* V,
                        int ldv, float beta, float* Q, int ldq);
 // Q = (dK/dlog sigma)(Pr, Pc) v, one column
 int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc,

@@ -116,7 +116,7 @@ template <int D, int NRHS, int R>
 __global__ void __launch_bounds__(KM_THREADS, 4)
 k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
        const float* __restrict__ V, int ldv, int tiles_per_split, float beta,
-       float* __restrict__ Q, int ldq, float* __restrict__ part) {
+       float* __restrict__ Q, int ldq, double* __restrict__ part) {
     constexpr int PS = (D + 1 + 3) / 4 * 4;
     constexpr int PS4 = PS / 4;
     __shared__ float4 sP[KM_BN * PS4];
@@ -127,7 +127,8 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
 
     float xi[R][D];
     float ai[R];
-    float acc[R][NRHS];
+    float acc[R][NRHS];     // one column tile, FP32
+    double acc64[R][NRHS];  // tiles folded in FP64: smooth kernels cancel heavily across tiles
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const long long i = row0 + r * KM_THREADS + tid;
@@ -136,7 +137,7 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
         for (int c = 0; c < D; ++c) xi[r][c] = ok ? 2.f * Pr[i * PS + c] : 0.f;
         ai[r] = ok ? Pr[i * PS + D] : 0.f;
 #pragma unroll
-        for (int q = 0; q < NRHS; ++q) acc[r][q] = 0.f;
+        for (int q = 0; q < NRHS; ++q) acc[r][q] = 0.f, acc64[r][q] = 0.0;
     }
 
     const int ntiles = (nc + KM_BN - 1) / KM_BN;
@@ -192,6 +193,10 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) acc64[r][q] += (double)acc[r][q], acc[r][q] = 0.f;
     }
 
 #pragma unroll
@@ -202,29 +207,29 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
                 Q[(size_t)q * ldq + i] =
-                    acc[r][q] + (beta != 0.f ? beta * V[(size_t)q * ldv + i] : 0.f);
+                    (float)(acc64[r][q] + (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
         } else {
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
-                part[((size_t)blockIdx.y * NRHS + q) * nr + i] = acc[r][q];
+                part[((size_t)blockIdx.y * NRHS + q) * nr + i] = acc64[r][q];
         }
     }
 }
 
-__global__ void k_kmvm_reduce(const float* __restrict__ part, int splits, int nr, int nrhs,
+__global__ void k_kmvm_reduce(const double* __restrict__ part, int splits, int nr, int nrhs,
                               const float* __restrict__ V, int ldv, float beta,
                               float* __restrict__ Q, int ldq) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)nr * nrhs) return;
     const int q = (int)(e / nr);
     const int i = (int)(e - (long long)q * nr);
-    float s = 0.f;
+    double s = 0.0;
     for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * nrhs + q) * nr + i];
-    if (beta != 0.f) s += beta * V[(size_t)q * ldv + i];
-    Q[(size_t)q * ldq + i] = s;
+    if (beta != 0.f) s += (double)beta * V[(size_t)q * ldv + i];
+    Q[(size_t)q * ldq + i] = (float)s;
 }
 
-int launch_kmvm_reduce(krr_ctx* ctx, const float* part, int splits, int nr, int nrhs, const float* V,
+int launch_kmvm_reduce(krr_ctx* ctx, const double* part, int splits, int nr, int nrhs, const float* V,
                        int ldv, float beta, float* Q, int ldq) {
     const long long tot = (long long)nr * nrhs;
     k_kmvm_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, splits, nr, nrhs, V, ldv, beta, Q,
@@ -233,13 +238,23 @@ int launch_kmvm_reduce(krr_ctx* ctx, const float* part, int splits, int nr, int 
     return KRR_OK;
 }
 
+// Rows per thread: the largest R whose live registers (R x (D + 1) coordinates, R x NRHS
+// FP32 tile sums plus their FP64 fold, one column's values) fit the 128 a thread has at
+// four blocks per SM.
+template <int D, int NRHS, int R>
+constexpr bool kmvm_fits() {
+    return R * (D + 1 + 3 * NRHS) + NRHS + 20 <= 128;
+}
 template <int D, int NRHS>
 constexpr int kmvm_rows() {
-    return (D > 32) ? 1 : (D > 16 || NRHS >= 16 || (NRHS >= 8 && D >= 8)) ? 2 : 4;
+    return (D > 32) ? 1
+           : (D <= 16 && kmvm_fits<D, NRHS, 4>()) ? 4
+           : kmvm_fits<D, NRHS, 2>() ? 2
+                                     : 1;
 }
 
 typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float,
-                        float*, int, float*);
+                        float*, int, double*);
 
 template <int D, int NRHS>
 static kmvm_fn pick2() {
@@ -327,7 +342,7 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         int splits = choose_splits(nblk, ntiles, slots);
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
-        float* part = nullptr;
+        double* part = nullptr;
         if (splits > 1)
             KRR_RET(bufT(ctx, "kmvm_part", (size_t)splits * chunk * nr, &part));
         dim3 grid(nblk, splits);
@@ -355,7 +370,7 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
 template <int D, int R>
 __global__ void __launch_bounds__(KM_THREADS, 4)
 k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
-              const float* __restrict__ V, int tiles_per_split, float* __restrict__ part) {
+              const float* __restrict__ V, int tiles_per_split, double* __restrict__ part) {
     constexpr int PS = (D + 1 + 3) / 4 * 4;
     constexpr int PS4 = PS / 4;
     __shared__ float4 sP[KM_BN * PS4];
@@ -363,6 +378,7 @@ k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc
     const int tid = threadIdx.x;
     const long long row0 = (long long)blockIdx.x * (KM_THREADS * R);
     float xi[R][D], ai[R], acc[R];
+    double acc64[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const long long i = row0 + r * KM_THREADS + tid;
@@ -371,6 +387,7 @@ k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc
         for (int c = 0; c < D; ++c) xi[r][c] = ok ? 2.f * Pr[i * PS + c] : 0.f;
         ai[r] = ok ? Pr[i * PS + D] : 0.f;
         acc[r] = 0.f;
+        acc64[r] = 0.0;
     }
     const int ntiles = (nc + KM_BN - 1) / KM_BN;
     const int t0 = blockIdx.y * tiles_per_split;
@@ -406,16 +423,18 @@ k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc64[r] += (double)acc[r], acc[r] = 0.f;
     }
-    const float scale = -2.f * 0.6931471805599453f;
+    const double scale = -2.0 * 0.6931471805599453;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const long long i = row0 + r * KM_THREADS + tid;
-        if (i < nr) part[(size_t)blockIdx.y * nr + i] = scale * acc[r];
+        if (i < nr) part[(size_t)blockIdx.y * nr + i] = scale * acc64[r];
     }
 }
 
-typedef void (*dsig_fn)(const float*, int, const float*, int, const float*, int, float*);
+typedef void (*dsig_fn)(const float*, int, const float*, int, const float*, int, double*);
 
 static dsig_fn dsig_pick(int dk) {
     switch (dk) {
@@ -442,7 +461,7 @@ int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float*
     int splits = choose_splits(nblk, ntiles, slots);
     const int tps = (ntiles + splits - 1) / splits;
     splits = (ntiles + tps - 1) / tps;
-    float* part;
+    double* part;
     KRR_RET(bufT(ctx, "dsig_part", (size_t)splits * nr, &part));
     fn<<<dim3(nblk, splits), KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, V, tps, part);
     KRR_CHECK_LAUNCH();
@@ -464,7 +483,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
     const bool same = (Xr == Xc && nr == nc);
     const int nblk_mean = (int)std::min<long long>(2LL * num_sms, ceil_div(nc, 256));
     // split-K layout of every right-hand-side chunk, as the context path chooses it
-    size_t part_floats = 0;
+    size_t part_elems = 0;
     for (int done = 0; done < nrhs;) {
         const int left = nrhs - done;
         const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
@@ -480,7 +499,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
         int splits = choose_splits(nblk, ntiles, num_sms * occ);
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
-        if (splits > 1) part_floats = std::max(part_floats, (size_t)splits * chunk * (size_t)nr);
+        if (splits > 1) part_elems = std::max(part_elems, (size_t)splits * chunk * (size_t)nr);
         done += chunk;
     }
     const size_t off_mpart = 0;
@@ -488,7 +507,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
     const size_t off_pc = off_mu + align256(sizeof(double) * d);
     const size_t off_pr = off_pc + align256(sizeof(float) * (size_t)nc * ps);
     const size_t off_part = off_pr + (same ? 0 : align256(sizeof(float) * (size_t)nr * ps));
-    const size_t total = off_part + align256(sizeof(float) * part_floats);
+    const size_t total = off_part + align256(sizeof(double) * part_elems);
     if (needed) *needed = total;
     if (total > cap) return KRR_E_INVAL;
 
@@ -496,7 +515,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
     double* mu = reinterpret_cast<double*>(scratch + off_mu);
     float* Pc = reinterpret_cast<float*>(scratch + off_pc);
     float* Pr = same ? Pc : reinterpret_cast<float*>(scratch + off_pr);
-    float* part = reinterpret_cast<float*>(scratch + off_part);
+    double* part = reinterpret_cast<double*>(scratch + off_part);
     const double s = 1.4426950408889634 / (2.0 * sigma * sigma);
     k_mean_partial<<<nblk_mean, 256, 0, stream>>>(Xc, nc, d, mpart);
     k_mean_final<<<1, 64, 0, stream>>>(mpart, nblk_mean, d, nc, mu);

@@ -263,7 +263,7 @@ template <int NRHS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
           int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
-          int tiles_per_split, float* __restrict__ part, int* __restrict__ err) {
+          int tiles_per_split, double* __restrict__ part, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const uint32_t tileA = 128u * Kp * 2u;            // bytes of one 128-row feature tile
     unsigned char* sA = smem;                         // 2 tiles (256 rows)
@@ -368,10 +368,13 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             const int t1 = min(t0 + tiles_per_split, ntiles);
             constexpr int NA = NRHS >= 8 ? 1 : 4;    // independent FMA chains per right-hand side
             float acc[NRHS][NA];
+            double acc64[NRHS];                      // tiles folded in FP64 (cancellation)
 #pragma unroll
-            for (int q = 0; q < NRHS; ++q)
+            for (int q = 0; q < NRHS; ++q) {
+                acc64[q] = 0.0;
 #pragma unroll
                 for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
+            }
             bool ok = true;
             for (int t = t0; t < t1; ++t, ++g) {
                 const int s = g % TC_NS, b = g & 1;
@@ -382,43 +385,51 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 const float* v = sV + s * NRHS * TC_BN + cgrp * 64;
                 const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) +
                                     (uint32_t)(b * 256 + half * 128 + cgrp * 64);
-                uint32_t r0[32], r1[32];
-                tmem_ld32(tb, r0);
-                tmem_ld32(tb + 32, r1);
-                tmem_wait_ld();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
+                // two 32-column halves: 32 live registers for the exponents instead of 64
 #pragma unroll
-                for (int j4 = 0; j4 < 16; ++j4) {
-                    float ev[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int c = 4 * j4 + u;
-                        ev[u] = ex2f(__uint_as_float(c < 32 ? r0[c] : r1[c - 32]));
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t r0[32];
+                    tmem_ld32(tb + 32 * hh, r0);
+                    tmem_wait_ld();
+                    if (hh == 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
                     }
 #pragma unroll
-                    for (int q = 0; q < NRHS; ++q) {
-                        const float4 vv = *reinterpret_cast<const float4*>(v + q * TC_BN + 4 * j4);
-                        acc[q][0 % NA] = fmaf(ev[0], vv.x, acc[q][0 % NA]);
-                        acc[q][1 % NA] = fmaf(ev[1], vv.y, acc[q][1 % NA]);
-                        acc[q][2 % NA] = fmaf(ev[2], vv.z, acc[q][2 % NA]);
-                        acc[q][3 % NA] = fmaf(ev[3], vv.w, acc[q][3 % NA]);
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        float ev[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) ev[u] = ex2f(__uint_as_float(r0[4 * j4 + u]));
+#pragma unroll
+                        for (int q = 0; q < NRHS; ++q) {
+                            const float4 vv =
+                                *reinterpret_cast<const float4*>(v + q * TC_BN + 32 * hh + 4 * j4);
+                            acc[q][0 % NA] = fmaf(ev[0], vv.x, acc[q][0 % NA]);
+                            acc[q][1 % NA] = fmaf(ev[1], vv.y, acc[q][1 % NA]);
+                            acc[q][2 % NA] = fmaf(ev[2], vv.z, acc[q][2 % NA]);
+                            acc[q][3 % NA] = fmaf(ev[3], vv.w, acc[q][3 % NA]);
+                        }
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->s_empty[s]);   // V of this stage consumed
-            }
-            if (!ok) break;
-            const long long row = (long long)rb * TC_ROWS + lrow;
-            if (row < nr) {
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q) {
                     float tot = acc[q][0];
 #pragma unroll
                     for (int a = 1; a < NA; ++a) tot += acc[q][a];
-                    part[(((size_t)sp * 2 + cgrp) * NRHS + q) * nr + row] = tot;
+                    acc64[q] += (double)tot;
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
                 }
+            }
+            if (!ok) break;
+            const long long row = (long long)rb * TC_ROWS + lrow;
+            if (row < nr) {
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q)
+                    part[(((size_t)sp * 2 + cgrp) * NRHS + q) * nr + row] = acc64[q];
             }
         }
     }
@@ -678,7 +689,7 @@ size_t tc_feature_bytes(long long n, int d) {
 }
 
 typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
-                      int, int, int, float*, int*);
+                      int, int, int, double*, int*);
 
 int choose_splits_public(int nblk, int ntiles, int slots);
 
@@ -713,7 +724,7 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
         const int items = nrb * splits;
-        float* part;
+        double* part;
         KRR_RET(bufT(ctx, "tc_part", (size_t)2 * splits * chunk * nr, &part));
         const int grid = std::min(items, ctx->num_sms);
         fn<<<grid, TC_THREADS, smem_launch, ctx->stream>>>(FA, FB, Kp, (int)nr, (int)nc, ncp, Vp, items,
