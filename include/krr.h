@@ -64,13 +64,18 @@ typedef struct krr_opts {
     double anchor_rtol;   /* pivots with |R_jj| < anchor_rtol |R_11| are dropped (1e-5)  */
     int    precision;     /* kernel product of the PCG iterations: 0 = FP32 FFMA tiles
                              (default); 1 = tcgen05 tensor cores, exponent from a BF16x3
-                             split GEMM (d <= 16; larger d uses the FP32 tiles)          */
+                             split GEMM (d <= 16; larger d uses the FP32 tiles);
+                             2 = FP32 FFMA tiles on exact coordinate differences
+                             (slower, no cancellation in the exponent)                   */
     int    residual;      /* refinement residual: 0 float-float on the FP32 pipe
                              (default), 1 FP64 pipe                                      */
     double pivot_tol;     /* the anchor set ends at the first anchor whose Cholesky pivot
                              in K_SS (its variance given the earlier anchors; K_SS has a
                              unit diagonal) is <= pivot_tol (default 1e-6)              */
-    int    reserved[4];
+    int    escalate;      /* 1 (default): when PCG meets non-positive curvature, or the
+                             true residual stops falling, on precision 0 or 1, switch the
+                             product to precision 2 and restart from the current alpha  */
+    int    reserved[3];
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -86,7 +91,12 @@ typedef struct krr_solve_info {
     int    sweep_iters[8];                /* PCG iterations before each replacement   */
     double sweep_residual[8];             /* worst column's true residual at the start
                                              and after each replacement                */
-    int    reserved[7];
+    int    product_form;                  /* precision of the product at the end (0-2)  */
+    int    restarts;                      /* times the CG direction was reset: at an
+                                             escalation, after a stall, or when a true
+                                             residual came out well above the recursive
+                                             one                                       */
+    int    reserved[5];
 } krr_solve_info;
 
 /* Fill *opts with the defaults.  Returns KRR_E_INVAL if opts is NULL. */
@@ -134,7 +144,10 @@ int krr_peak_probe(int kind, double* ops_per_s, void* stream);
  * mean of Xc; K is never stored.  Each thread sums one 128-column tile in
  * FP32 and folds the tile sums in FP64 (smooth kernels with mixed-sign V cancel
  * heavily, and an FP32 running sum over 10^5 columns loses about beta of the
- * result).  beta must be 0 unless nr == nc (square
+ * result).  With opts.precision = 2 the exponent is instead -||xr_i - xc_j||^2
+ * / (2 sigma^2) from the differences of the given coordinates (no centring), and
+ * with opts.precision = 1 (d <= 16) it is the tensor-core BF16x3 split GEMM.
+ * beta must be 0 unless nr == nc (square
  * product with the ridge term).  Xr may equal Xc.
  * ------------------------------------------------------------------------- */
 int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long long nc,
@@ -228,7 +241,8 @@ int krr_kmvm_noalloc(const float* Xr, long long nr, const float* Xc, long long n
                      double sigma, double beta, const float* V, int nrhs, float* Q, void* stream,
                      unsigned long long* scratch_needed);
 
-/* f = K(Xtest, X) alpha (Eq. (1)); Xtest m x d, alpha n x nrhs FP32, f m x nrhs. */
+/* f = K(Xtest, X) alpha (Eq. (1)); Xtest m x d, alpha n x nrhs FP32, f m x nrhs.
+ * FP32 tiles, in the exact-difference form when opts.precision = 2. */
 int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alpha, int nrhs,
                 float* f);
 

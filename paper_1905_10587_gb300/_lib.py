@@ -26,14 +26,15 @@ class KrrOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("refine_max", C.c_int), ("oversample", C.c_int),
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
-                ("reserved", C.c_int * 4)]
+                ("escalate", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class KrrSolveInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("sweeps", C.c_int), ("k_eff", C.c_int),
                 ("rel_residual", C.c_double * KRR_MAX_RHS), ("build_ms", C.c_double),
                 ("solve_ms", C.c_double), ("mvm_count", C.c_int), ("sweep_iters", C.c_int * 8),
-                ("sweep_residual", C.c_double * 8), ("reserved", C.c_int * 7)]
+                ("sweep_residual", C.c_double * 8), ("product_form", C.c_int),
+                ("restarts", C.c_int), ("reserved", C.c_int * 5)]
 
 
 _vp, _i, _ll, _d, _ull = C.c_void_p, C.c_int, C.c_longlong, C.c_double, C.c_ulonglong

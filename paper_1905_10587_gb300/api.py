@@ -201,7 +201,8 @@ class KRR:
                    rel_residual=[info.rel_residual[i] for i in range(Yt.shape[0])],
                    build_ms=info.build_ms, solve_ms=info.solve_ms, mvm_count=info.mvm_count,
                    sweep_iters=[info.sweep_iters[i] for i in range(min(8, info.sweeps + 1))],
-                   sweep_residual=[info.sweep_residual[i] for i in range(min(8, info.sweeps + 1))])
+                   sweep_residual=[info.sweep_residual[i] for i in range(min(8, info.sweeps + 1))],
+                   product_form=info.product_form, restarts=info.restarts)
         return _uncols(A, vec), out
 
     def grad(self, y, Xval, yval, tol: float = 1e-8):

@@ -238,10 +238,26 @@ static int build_from_anchors(krr_ctx* ctx, const int* S_dev, int k_eff) {
 
 static bool use_tc(const krr_ctx* ctx, int d) { return ctx->opts.precision == 1 && kernel_dim(d) <= 16; }
 
-// (K + beta I) V for the built point set, on the path opts.precision selects.
-static int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q) {
-    if (ctx->FA)
+// Raw coordinates of the built point set in the packed layout (mu = 0, s = 1), made once.
+static int ensure_raw_points(krr_ctx* ctx) {
+    if (ctx->Praw) return KRR_OK;
+    double* mu0;
+    KRR_RET(bufT(ctx, "mu0", (size_t)ctx->d, &mu0));
+    KRR_TRY_CUDA(cudaMemsetAsync(mu0, 0, sizeof(double) * ctx->d, ctx->stream));
+    KRR_RET(bufT(ctx, "Praw", (size_t)ctx->n * ctx->ps, &ctx->Praw));
+    return launch_pack(ctx, ctx->X, ctx->n, ctx->d, mu0, 1.0, ctx->Praw);
+}
+
+// (K + beta I) V for the built point set in product form 0 (FP32 expansion), 1 (tensor
+// cores, when built) or 2 (FP32 on raw coordinate differences).
+static int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q, int form) {
+    if (form == 1 && ctx->FA)
         return launch_kmvm_tc(ctx, ctx->FA, ctx->n, ctx->FB, ctx->n, ctx->d, (float)ctx->beta, V, nrhs, Q);
+    if (form == 2) {
+        KRR_RET(ensure_raw_points(ctx));
+        return launch_kmvm(ctx, ctx->Praw, ctx->n, ctx->Praw, ctx->n, ctx->d, (float)ctx->beta, V, nrhs,
+                           Q, (float)(-ctx->s));
+    }
     return launch_kmvm(ctx, ctx->P, ctx->n, ctx->P, ctx->n, ctx->d, (float)ctx->beta, V, nrhs, Q);
 }
 
@@ -262,6 +278,7 @@ static int build_common(krr_ctx* ctx, const float* X, long long n, int d, double
     KRR_RET(launch_mean(ctx, X, n, d, mu));
     KRR_RET(launch_pack(ctx, X, n, d, mu, ctx->s, ctx->P));
     ctx->FA = ctx->FB = nullptr;
+    ctx->Praw = nullptr;
     if (use_tc(ctx, d)) {
         KRR_RET(bufT(ctx, "tc_FA", tc_feature_bytes(n, d), &ctx->FA));
         KRR_RET(bufT(ctx, "tc_FB", tc_feature_bytes(n, d), &ctx->FB));
@@ -288,6 +305,7 @@ int krr_default_opts(krr_opts* o) {
     o->anchor_rtol = 1e-5;
     o->pivot_tol = 1e-6;
     o->precision = 0;
+    o->escalate = 1;
     return KRR_OK;
 }
 
@@ -300,7 +318,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
     if (ctx->opts.max_iter < 1 || ctx->opts.refine_max < 1 || ctx->opts.oversample < 0 ||
         ctx->opts.check_every < 1 || !(ctx->opts.inner_tol > 0.0) || ctx->opts.inner_tol >= 1.0 ||
         ctx->opts.residual < 0 || ctx->opts.residual > 1 || ctx->opts.precision < 0 ||
-        ctx->opts.precision > 1 ||
+        ctx->opts.precision > 2 || ctx->opts.escalate < 0 || ctx->opts.escalate > 1 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -390,10 +408,22 @@ int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long 
     if (beta != 0.0 && nr != nc) return fail(ctx, KRR_E_INVAL, "beta needs a square product");
     const int ps = packed_stride(d);
     const double s = LOG2E / (2.0 * sigma * sigma);
+    const bool raw = ctx->opts.precision == 2;
     double* mu;
     float *Pc, *Pr;
     KRR_RET(bufT(ctx, "kmvm_mu", (size_t)d, &mu));
     KRR_RET(bufT(ctx, "kmvm_Pc", (size_t)nc * ps, &Pc));
+    if (raw) {
+        // exact-difference form: raw coordinates (mu = 0, unit scale)
+        KRR_TRY_CUDA(cudaMemsetAsync(mu, 0, sizeof(double) * d, ctx->stream));
+        KRR_RET(launch_pack(ctx, Xc, nc, d, mu, 1.0, Pc));
+        Pr = Pc;
+        if (!(Xr == Xc && nr == nc)) {
+            KRR_RET(bufT(ctx, "kmvm_Pr", (size_t)nr * ps, &Pr));
+            KRR_RET(launch_pack(ctx, Xr, nr, d, mu, 1.0, Pr));
+        }
+        return launch_kmvm(ctx, Pr, nr, Pc, nc, d, (float)beta, V, nrhs, Q, (float)(-s));
+    }
     KRR_RET(launch_mean(ctx, Xc, nc, d, mu));
     KRR_RET(launch_pack(ctx, Xc, nc, d, mu, s, Pc));
     if (Xr == Xc && nr == nc) {
@@ -586,6 +616,10 @@ int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out) {
     return launch_apply_precond(ctx, In, nrhs, Out, nullptr);
 }
 
+// A replacement whose true residual norm exceeds twice the recursive one restarts the
+// recurrence (squared norms compared).
+static constexpr double kGapRestart2 = 4.0;
+
 int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol, double* alpha,
               krr_solve_info* info) {
     if (!ctx) return KRR_E_INVAL;
@@ -677,11 +711,14 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         return false;
     };
 
-    KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
-    KRR_RET(true_residual(true));
-    if (!any_active()) {
-        status = KRR_OK;
-    } else {
+    // Product form: the requested one, and the exact-difference FP32 form after an
+    // escalation.  The expansion forms (0, 1) round a_i + a_j + 2 x_i.x_j, which costs
+    // about eps (|a_i| + |a_j|) per entry; when lambda_max(K) / beta approaches 1/eps that
+    // perturbation is as large as beta I: the FP32 operator then meets non-positive
+    // curvature, or stops reducing the true residual, and form 2 takes over.
+    int form = ctx->opts.precision == 1 ? (ctx->FA ? 1 : 0) : ctx->opts.precision;
+    // (Re)start the recurrence from the current r: z = M^-1 r, p = z.
+    auto restart_cg = [&]() -> int {
         {
             Phase ph(ctx, PH_APPLY);
             KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part1));
@@ -689,11 +726,27 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         KRR_RET(launch_cg_start(ctx, r, z, nrhs, part1, part2));
         KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
         KRR_TRY_CUDA(cudaMemcpyAsync(p, z, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
-        int it = 0, since = 0;
+        return KRR_OK;
+    };
+
+    KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+    KRR_RET(true_residual(true));
+    if (!any_active()) {
+        status = KRR_OK;
+    } else {
+        KRR_RET(restart_cg());
+        int it = 0, since = 0, gapped = 0;
+        // Stall watch: `window` = 3x the length of the first cycle (at least 100); if the
+        // worst column's true residual has not halved within a window, the product's
+        // error is what limits the solve.  A replacement is forced once per window so
+        // that a stalled column is measured even when no column triggers one.
+        int window = ctx->opts.max_iter, it_best = 0;
+        double best = 1.0;
+        std::vector<double> rec(nrhs);
         while (true) {
             {
                 Phase ph(ctx, PH_KMVM);
-                KRR_RET(square_product(ctx, p, nrhs, q));
+                KRR_RET(square_product(ctx, p, nrhs, q, form));
             }
             inf.mvm_count++;
             {
@@ -708,26 +761,66 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                 KRR_TRY_CUDA(cudaMemcpyAsync(ctx->cg_host, ctx->cg, sizeof(CGScalars),
                                              cudaMemcpyDeviceToHost, ctx->stream));
                 KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+                bool escalate = false;
                 if (ctx->cg_host->bad) {
-                    fail(ctx, KRR_E_NONFINITE, "non-positive curvature or non-finite value in PCG");
-                    break;
+                    if (!ctx->opts.escalate || form == 2 || last) {
+                        fail(ctx, KRR_E_NONFINITE, "non-positive curvature or non-finite value in PCG");
+                        break;
+                    }
+                    escalate = true;
                 }
-                bool update = last;
+                bool update = last || escalate || since >= window;
                 for (int c = 0; c < nrhs; ++c) {
                     if (!act[c]) continue;
                     const double rr = ctx->cg_host->rr[c];
+                    rec[c] = rr;
                     if (rr <= delta2 * rtrue[c] || rr <= 0.25 * tol * tol * yn[c]) update = true;
                 }
                 if (update) {
                     if (inf.sweeps < 8) inf.sweep_iters[inf.sweeps] = since;
+                    if (inf.sweeps == 0) window = std::max(100, 3 * since);
                     inf.sweeps++;
                     since = 0;
+                    std::vector<int> was(act);
                     KRR_RET(true_residual(false));
                     if (!any_active()) {
                         status = KRR_OK;
                         break;
                     }
                     if (last || inf.sweeps >= ctx->opts.refine_max) break;
+                    // A true residual well above the recursive one means the FP32 operator,
+                    // not rounding in the recurrence, set the gap: the old direction is then
+                    // no longer conjugate for this residual, so the recurrence restarts.
+                    bool restart = escalate;
+                    for (int c = 0; c < nrhs; ++c)
+                        if (was[c] && act[c] && !escalate && rtrue[c] > kGapRestart2 * rec[c])
+                            restart = true;
+                    // two gapped replacements in a row, or a stall: the product's own error,
+                    // not the recurrence, limits the solve; move to the exact-difference form
+                    gapped = restart ? gapped + 1 : 0;
+                    double w = 0.0;
+                    for (int c = 0; c < nrhs; ++c) w = std::max(w, inf.rel_residual[c]);
+                    if (w < 0.5 * best) {
+                        best = w;
+                        it_best = it;
+                    }
+                    const bool stalled = it - it_best > window;
+                    if (ctx->opts.escalate && form != 2 && (gapped >= 2 || escalate || stalled)) {
+                        form = 2;
+                        restart = true;
+                        gapped = 0;
+                        it_best = it;
+                        best = w;
+                    } else if (stalled) {
+                        restart = true;   // already exact differences: fresh direction
+                        it_best = it;
+                        best = w;
+                    }
+                    if (restart) {
+                        inf.restarts++;
+                        KRR_RET(restart_cg());
+                        continue;
+                    }
                     KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
                 }
             }
@@ -748,6 +841,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     }
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     inf.status = status;
+    inf.product_form = form;
     inf.solve_ms = now_ms() - t0;
     if (info) *info = inf;
     if (status != KRR_OK) fail(ctx, status, "tolerance not reached");
@@ -847,6 +941,12 @@ int krr_predict(krr_ctx* ctx, const float* Xtest, long long m, const float* alph
     float* Pt;
     double* mu;
     KRR_RET(bufT(ctx, "pred_P", (size_t)m * ctx->ps, &Pt));
+    if (ctx->opts.precision == 2) {
+        KRR_RET(ensure_raw_points(ctx));
+        KRR_RET(bufT(ctx, "mu0", (size_t)ctx->d, &mu));
+        KRR_RET(launch_pack(ctx, Xtest, m, ctx->d, mu, 1.0, Pt));
+        return launch_kmvm(ctx, Pt, m, ctx->Praw, ctx->n, ctx->d, 0.f, alpha, nrhs, f, (float)(-ctx->s));
+    }
     KRR_RET(bufT(ctx, "mu", (size_t)ctx->d, &mu));
     KRR_RET(launch_pack(ctx, Xtest, m, ctx->d, mu, ctx->s, Pt));
     return launch_kmvm(ctx, Pt, m, ctx->P, ctx->n, ctx->d, 0.f, alpha, nrhs, f);

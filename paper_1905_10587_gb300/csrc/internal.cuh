@@ -102,6 +102,7 @@ struct krr_ctx {
     double build_ms = 0;
     // device arrays (views into bufs)
     float* P = nullptr;        // n x ps packed points of X
+    float* Praw = nullptr;     // n x ps raw coordinates of X (difference form), on demand
     float* PS = nullptr;       // k_eff x ps packed anchors
     float* XS = nullptr;       // k_eff x d raw anchor coordinates
     int* S = nullptr;          // k_eff anchor indices
@@ -172,9 +173,11 @@ int launch_pack(krr_ctx* ctx, const float* X, long long n, int d, const double* 
                 float* P);
 int launch_gather_pack(krr_ctx* ctx, const float* P, int ps, const float* X, int d, const int* idx,
                        int m, float* Pout, float* Xout);
-// Q = K(Pr, Pc) V + beta V (RHS-major, V: nc x nrhs, Q: nr x nrhs)
+// Q = K(Pr, Pc) V + beta V (RHS-major, V: nc x nrhs, Q: nr x nrhs).  raw_nsc = 0: Pr, Pc
+// are packed [xh, a] points (expansion form); raw_nsc = -s: they are the raw coordinates
+// packed with mu = 0 and s = 1 and the exponent is raw_nsc * ||x_i - x_j||^2.
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
-                float beta, const float* V, int nrhs, float* Q);
+                float beta, const float* V, int nrhs, float* Q, float raw_nsc = 0.f);
 // R = Y - (K + beta I) A in FP64 (Y float, A/R double)
 int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);

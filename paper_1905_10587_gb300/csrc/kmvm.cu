@@ -112,10 +112,15 @@ int launch_gather_pack(krr_ctx* ctx, const float* P, int ps, const float* X, int
 constexpr int KM_THREADS = 128;
 constexpr int KM_BN = 128;
 
-template <int D, int NRHS, int R>
+// RAW = false: packed points [xh, a] and the expansion a_i + a_j + 2 xh_i . xh_j.
+// RAW = true: packed points are the caller's coordinates unchanged and the exponent is
+// nsc * sum_c (x_ic - x_jc)^2 with nsc = -s: no centring, scaling or norm is rounded
+// per point, so the only per-entry errors are those of the differences, the squares
+// and the exponential (about eps |t|) instead of eps (|a_i| + |a_j| + 2 |xh_i . xh_j|).
+template <int D, int NRHS, int R, bool RAW>
 __global__ void __launch_bounds__(KM_THREADS, 4)
 k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
-       const float* __restrict__ V, int ldv, int tiles_per_split, float beta,
+       const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc,
        float* __restrict__ Q, int ldq, double* __restrict__ part) {
     constexpr int PS = (D + 1 + 3) / 4 * 4;
     constexpr int PS4 = PS / 4;
@@ -134,8 +139,8 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
         const long long i = row0 + r * KM_THREADS + tid;
         const bool ok = i < nr;
 #pragma unroll
-        for (int c = 0; c < D; ++c) xi[r][c] = ok ? 2.f * Pr[i * PS + c] : 0.f;
-        ai[r] = ok ? Pr[i * PS + D] : 0.f;
+        for (int c = 0; c < D; ++c) xi[r][c] = ok ? (RAW ? 1.f : 2.f) * Pr[i * PS + c] : 0.f;
+        ai[r] = (ok && !RAW) ? Pr[i * PS + D] : 0.f;
 #pragma unroll
         for (int q = 0; q < NRHS; ++q) acc[r][q] = 0.f, acc64[r][q] = 0.0;
     }
@@ -184,9 +189,20 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float tt = ai[r] + xj[D];
+                float tt;
+                if constexpr (RAW) {
+                    float ss = 0.f;
 #pragma unroll
-                for (int c = 0; c < D; ++c) tt = fmaf(xi[r][c], xj[c], tt);
+                    for (int c = 0; c < D; ++c) {
+                        const float df = xi[r][c] - xj[c];
+                        ss = fmaf(df, df, ss);
+                    }
+                    tt = ss * nsc;
+                } else {
+                    tt = ai[r] + xj[D];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) tt = fmaf(xi[r][c], xj[c], tt);
+                }
                 const float e = ex2f(tt);
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q) acc[r][q] = fmaf(e, vj[q], acc[r][q]);
@@ -253,30 +269,31 @@ constexpr int kmvm_rows() {
                                      : 1;
 }
 
-typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float,
+typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float, float,
                         float*, int, double*);
 
 template <int D, int NRHS>
-static kmvm_fn pick2() {
-    return &k_kmvm<D, NRHS, kmvm_rows<D, NRHS>()>;
+static kmvm_fn pick2(bool raw) {
+    return raw ? &k_kmvm<D, NRHS, kmvm_rows<D, NRHS>(), true>
+               : &k_kmvm<D, NRHS, kmvm_rows<D, NRHS>(), false>;
 }
 
 template <int D>
-static kmvm_fn pick1(int nrhs, int* R) {
+static kmvm_fn pick1(int nrhs, int* R, bool raw) {
     switch (nrhs) {
-        case 1: *R = kmvm_rows<D, 1>(); return pick2<D, 1>();
-        case 2: *R = kmvm_rows<D, 2>(); return pick2<D, 2>();
-        case 4: *R = kmvm_rows<D, 4>(); return pick2<D, 4>();
-        case 8: *R = kmvm_rows<D, 8>(); return pick2<D, 8>();
-        case 16: *R = kmvm_rows<D, 16>(); return pick2<D, 16>();
+        case 1: *R = kmvm_rows<D, 1>(); return pick2<D, 1>(raw);
+        case 2: *R = kmvm_rows<D, 2>(); return pick2<D, 2>(raw);
+        case 4: *R = kmvm_rows<D, 4>(); return pick2<D, 4>(raw);
+        case 8: *R = kmvm_rows<D, 8>(); return pick2<D, 8>(raw);
+        case 16: *R = kmvm_rows<D, 16>(); return pick2<D, 16>(raw);
     }
     return nullptr;
 }
 
-static kmvm_fn pick(int dk, int nrhs, int* R) {
+static kmvm_fn pick(int dk, int nrhs, int* R, bool raw = false) {
     switch (dk) {
 #define KRR_D(v) \
-    case v: return pick1<v>(nrhs, R);
+    case v: return pick1<v>(nrhs, R, raw);
         KRR_D(1) KRR_D(2) KRR_D(3) KRR_D(4) KRR_D(5) KRR_D(6) KRR_D(7) KRR_D(8)
         KRR_D(9) KRR_D(10) KRR_D(11) KRR_D(12) KRR_D(13) KRR_D(14) KRR_D(15) KRR_D(16)
         KRR_D(24) KRR_D(32) KRR_D(48) KRR_D(64)
@@ -324,7 +341,8 @@ static int choose_splits(int nblk, int ntiles, int slots) {
 int choose_splits_public(int nblk, int ntiles, int slots) { return choose_splits(nblk, ntiles, slots); }
 
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
-                float beta, const float* V, int nrhs, float* Q) {
+                float beta, const float* V, int nrhs, float* Q, float raw_nsc) {
+    const bool raw = raw_nsc != 0.f;
     if (nr > 0x7fffffffLL || nc > 0x7fffffffLL)
         return fail(ctx, KRR_E_INVAL, "kmvm: more than 2^31 points");
     const int dk = kernel_dim(d);
@@ -333,7 +351,7 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         const int left = nrhs - done;
         const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         int R = 4;
-        kmvm_fn fn = pick(dk, chunk, &R);
+        kmvm_fn fn = pick(dk, chunk, &R, raw);
         if (!fn) return fail(ctx, KRR_E_INVAL, "kmvm: unsupported dimension");
         const int rows_per = KM_THREADS * R;
         const int nblk = (int)ceil_div(nr, rows_per);
@@ -349,7 +367,7 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         const float* Vc = V + (size_t)done * nc;
         float* Qc = Q + (size_t)done * nr;
         fn<<<grid, KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps, beta,
-                                                 Qc, (int)nr, part);
+                                                 raw_nsc, Qc, (int)nr, part);
         KRR_CHECK_LAUNCH();
         if (splits > 1) {
             const long long tot = nr * chunk;
@@ -538,7 +556,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
         const float* Vc = V + (size_t)done * nc;
         float* Qc = Q + (size_t)done * nr;
         fn<<<dim3(nblk, splits), KM_THREADS, 0, stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps,
-                                                          (float)beta, Qc, (int)nr,
+                                                          (float)beta, 0.f, Qc, (int)nr,
                                                           splits > 1 ? part : nullptr);
         if (splits > 1)
             k_kmvm_reduce<<<ceil_div(nr * chunk, 256), 256, 0, stream>>>(part, splits, (int)nr, chunk,

@@ -1,0 +1,126 @@
+"""The exact-difference product form (precision 2) and the solver's escalation to it
+(needs a GB300).
+
+Form 2 evaluates exp(-||x_i - x_j||^2 / (2 sigma^2)) from differences of the given
+FP32 coordinates, so its per-entry error is about eps |t| instead of the expansion
+form's eps (|a_i| + |a_j| + 2 |x_i . x_j|); where lambda_max(K) / beta nears 1/eps
+only form 2 keeps the FP32 operator close enough to K + beta I.  Oracle: FP64
+products from the definition; tolerances as for the other forms (1e-5 per product
+column, 1e-6 final residual, 1e-4 on alpha against the dense FP64 solve).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import krr_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def _relcols(got, ref):
+    got = np.atleast_2d(np.asarray(got, dtype=np.float64).T).T
+    ref = np.atleast_2d(np.asarray(ref, dtype=np.float64).T).T
+    return np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+
+
+@pytest.mark.parametrize("n,d,nrhs,beta", [(1, 3, 1, 0.5), (127, 2, 3, 0.0), (777, 13, 5, 0.1),
+                                            (4099, 3, 16, 1e-4), (1000, 8, 8, 1e-3),
+                                            (300, 24, 2, 0.0), (130, 64, 1, 1.0)])
+def test_raw_product_square(n, d, nrhs, beta):
+    from paper_1905_10587_gb300.api import KRR
+    rng = np.random.Generator(np.random.PCG64(100 + n + d))
+    X = rng.uniform(0, 10, size=(n, d)).astype(np.float32)
+    V = rng.normal(size=(n, nrhs)).astype(np.float32)
+    sigma = 0.8 * np.sqrt(d / 3)
+    Q = KRR(precision=2).kmvm(_t(X), _t(X), _t(V), sigma, beta).cpu().numpy()
+    assert _relcols(Q, O.kmvm(X, V.astype(np.float64), sigma, beta)).max() <= 1e-5
+
+
+def test_raw_product_rectangular_and_offset():
+    # points far from the origin: the raw differences stay exact where they matter
+    from paper_1905_10587_gb300.api import KRR
+    rng = np.random.Generator(np.random.PCG64(77))
+    Xc = (rng.uniform(0, 4, size=(3001, 3)) + 500.0).astype(np.float32)
+    Xr = (rng.uniform(0, 4, size=(513, 3)) + 500.0).astype(np.float32)
+    V = rng.normal(size=(3001, 2)).astype(np.float32)
+    Q = KRR(precision=2).kmvm(_t(Xr), _t(Xc), _t(V), 0.7).cpu().numpy()
+    assert _relcols(Q, O.kmvm_rect(Xr, Xc, V.astype(np.float64), 0.7)).max() <= 1e-5
+
+
+def test_raw_entries_beat_the_expansion_on_a_wide_domain():
+    # U[0,10]^3 with sigma 0.8: the expansion rounds terms up to ~85 in log2 units, the
+    # raw form only the exponent itself; single entries are read out with V = e_j
+    from paper_1905_10587_gb300.api import KRR
+    rng = np.random.Generator(np.random.PCG64(5))
+    X = rng.uniform(0, 10, size=(2048, 3)).astype(np.float32)
+    cols = np.arange(0, 2048, 128)
+    V = np.zeros((2048, cols.size), np.float32)
+    V[cols, np.arange(cols.size)] = 1.0
+    ref = O.kernel_matrix(X.astype(np.float64), X[cols].astype(np.float64), 0.8)
+    near = ref > 1e-3
+    errs = {}
+    for prec in (0, 2):
+        Q = KRR(precision=prec).kmvm(_t(X), _t(X), _t(V), 0.8).cpu().numpy().astype(np.float64)
+        errs[prec] = np.max(np.abs(Q[near] - ref[near]) / ref[near])
+    assert errs[2] <= 2e-6
+    assert errs[2] < errs[0]
+
+
+def test_solve_in_raw_form_small_config():
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.small()
+    ctx = KRR(precision=2)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=3)
+    a, info = ctx.solve(_t(p.Y), tol=1e-6)
+    assert info["product_form"] == 2
+    a = a.cpu().numpy()
+    res = np.linalg.norm(O.residual(p.X, a, p.Y, p.sigma, p.beta)) / np.linalg.norm(p.Y)
+    assert res <= 1e-6
+    ref = O.solve_dense(p.X, p.Y.astype(np.float64), p.sigma, p.beta)
+    assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_predict_in_raw_form():
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.small(n=900)
+    rng = np.random.Generator(np.random.PCG64(8))
+    Xt = rng.uniform(0, 1, size=(257, p.d)).astype(np.float32)
+    ctx = KRR(precision=2)
+    ctx.build(_t(p.X), p.sigma, p.beta, 50, seed=1)
+    alpha = rng.normal(size=(p.n, 2)).astype(np.float32)
+    f = ctx.predict(_t(Xt), _t(alpha)).cpu().numpy()
+    assert _relcols(f, O.predict(Xt, p.X, alpha.astype(np.float64), p.sigma)).max() <= 1e-5
+
+
+def test_escalation_rescues_a_smooth_ill_conditioned_problem():
+    # one of the 64 batched problems (n = 21078, d = 10, sigma = sqrt(10), beta = 1e-3,
+    # 8 RHS): lambda_max / beta ~ 1e7, the FP32 expansion form stalls and the solver
+    # moves to form 2
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.batched()[8]
+    ctx = KRR(precision=0, max_iter=4000)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=9)
+    a, info = ctx.solve(_t(p.Y), tol=1e-6)
+    assert info["status"] == 0 and max(info["rel_residual"]) <= 1e-6
+    rows = np.random.Generator(np.random.PCG64(4)).choice(p.n, 24, replace=False)
+    A = a.cpu().numpy()
+    r = p.Y[rows].astype(np.float64) - O.kmvm(p.X, A, p.sigma, p.beta, rows=rows)
+    # sampled rows: their FP64 residual against the 1e-6 target scaled to 24 of n rows
+    # (10x slack for the sample), plus the oracle's own rounding of each sum
+    cond = O.kmvm(p.X, np.abs(A), p.sigma, p.beta, rows=rows)
+    bound = (10 * 1e-6 * np.linalg.norm(p.Y, axis=0) * np.sqrt(rows.size / p.n)
+             + 1e-13 * np.linalg.norm(cond, axis=0))
+    assert np.all(np.linalg.norm(r, axis=0) <= bound)
+
+
+def test_escalate_option_is_validated():
+    from paper_1905_10587_gb300.api import KRR, KRRError
+    with pytest.raises(KRRError):
+        KRR(escalate=2)
+    with pytest.raises(KRRError):
+        KRR(precision=3)
