@@ -736,11 +736,12 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     } else {
         KRR_RET(restart_cg());
         int it = 0, since = 0, gapped = 0;
-        // Stall watch: `window` = 3x the length of the first cycle (at least 100); if the
+        // Stall watch: `window` = 3x the length of the first cycle (at least 100; 500 until
+        // the first cycle ends, which also bounds that cycle before a true residual); if the
         // worst column's true residual has not halved within a window, the product's
         // error is what limits the solve.  A replacement is forced once per window so
         // that a stalled column is measured even when no column triggers one.
-        int window = ctx->opts.max_iter, it_best = 0;
+        int window = 500, it_best = 0;
         double best = 1.0;
         std::vector<double> rec(nrhs);
         while (true) {

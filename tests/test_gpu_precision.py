@@ -124,3 +124,15 @@ def test_escalate_option_is_validated():
         KRR(escalate=2)
     with pytest.raises(KRRError):
         KRR(precision=3)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_wide_cube_products_full_size_sampled(prec):
+    # the 10^6-point cube workload (U[0,10]^3, sigma 0.8, beta 1e-4) with y and 15
+    # N(0,1) columns: 64 sampled rows of (K + beta I) V against the oracle
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.cube3d(nrhs=16)
+    Q = KRR(precision=prec).kmvm(_t(p.X), _t(p.X), _t(p.Y), p.sigma, p.beta).cpu().numpy()
+    rows = np.random.Generator(np.random.PCG64(21)).choice(p.n, 64, replace=False)
+    ref = O.kmvm(p.X, p.Y.astype(np.float64), p.sigma, p.beta, rows=rows)
+    assert _relcols(Q[rows], ref).max() <= 1e-5
