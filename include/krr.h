@@ -124,11 +124,14 @@ int krr_profile_enable(krr_ctx* ctx, int on);
 int krr_profile_read(krr_ctx* ctx, const char* phase, double* total_ms, long long* count);
 
 /* Known-answer test of the tensor-core path's shared-memory and instruction
- * descriptors: one 128 x 32 x 16 BF16 tcgen05.mma of small integers, compared on
- * the host.  variant 0 is the layout the library uses (core matrices adjacent
- * along K 128 bytes apart), variant 1 swaps the two strides.  Writes the number of
- * wrong entries and the largest error (host outputs).  No counterpart in the paper:
- * a check of the hardware encoding the tensor-core product relies on. */
+ * descriptors: 128 x 32 BF16 tcgen05.mma products of small integers, compared on
+ * the host.  variant 0: one K = 16 step in the unswizzled core-matrix layout (the
+ * sketch's P and Omega operands); variant 1 swaps its two strides (must fail);
+ * variant 2: K = 64 in four steps in the 128-byte swizzled layout of the point
+ * features; variant 3 reads that data through an unswizzled descriptor (must fail).
+ * Writes the number of wrong entries and the largest error (host outputs).  No
+ * counterpart in the paper: a check of the hardware encoding the tensor-core
+ * product relies on. */
 int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream);
 
 /* Whole-GPU issue-rate probe used for roofline denominators: kind 0 = FP32 FFMA,

@@ -122,6 +122,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     d |= (uint64_t)1 << 46;
     return d;
 }
+// The same descriptor for the 128-byte swizzled K-major layout (mode 2 at bits 61-63):
+// rows of 128 bytes (64 BF16 along K), 8-row atoms of 1024 bytes at sbo = 1024, the
+// 16-byte chunk c of row r stored at chunk c ^ (r & 7).  The leading offset is unused
+// for this layout (field 1).  A K step of 16 elements inside the atom advances the
+// start address by 32 bytes; atoms must be 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9 and
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -133,26 +148,39 @@ __host__ __device__ inline uint32_t tile_off(int r, int k, int Kp) {
     return (uint32_t)((((r >> 3) * (Kp >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
+// Byte offset of element (r, k) in a feature tile of `rows` rows in the 128-byte swizzled
+// layout: K in slabs of 64 (slab-major, each slab rows x 128 bytes), then the swizzle.
+__host__ __device__ inline uint32_t tile_off_sw(int r, int k, int rows) {
+    const uint32_t lin = (uint32_t)(k >> 6) * (uint32_t)rows * 128u + (uint32_t)r * 128u + (uint32_t)(k & 63) * 2u;
+    return lin ^ (((lin >> 7) & 7u) << 4);
+}
+
 // ------------------------------------------------------------------ self-test
-// One M=128, N=32, K=16 MMA on small integers (exact in BF16 and FP32); out[r*32 + c]
-// receives D.  variant 0 uses lbo = 128 (K neighbours), sbo = 256 (row groups);
-// variant 1 swaps them.  Every address stays inside the 5 KB of operands.
+// M=128, N=32 MMAs on small integers (exact in BF16 and FP32); out[r*32 + c] receives D.
+// variant 0: one K=16 step in the core-matrix layout, lbo = 128 (K neighbours), sbo = 256
+// (row groups); variant 1 swaps them; variant 2: K = 64 in four steps in the 128-byte
+// swizzled layout (the feature layout); variant 3 reads that swizzled data through an
+// unswizzled descriptor.  Every address stays inside the 20 KB of operands.
 __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restrict__ out,
                                                      int* __restrict__ err) {
-    __shared__ __align__(1024) unsigned char sA[128 * 16 * 2];
-    __shared__ __align__(1024) unsigned char sB[32 * 16 * 2];
+    __shared__ __align__(1024) unsigned char sA[128 * 64 * 2];
+    __shared__ __align__(1024) unsigned char sB[32 * 64 * 2];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tbase;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < 128 * 16; e += 128) {
-        const int r = e / 16, k = e % 16;
+    const bool sw = variant >= 2;
+    const int K = sw ? 64 : 16;
+    for (int e = tid; e < 128 * K; e += 128) {
+        const int r = e / K, k = e % K;
         const float v = (float)((r % 7) - 3 + (k % 3));
-        *reinterpret_cast<__nv_bfloat16*>(sA + tile_off(r, k, 16)) = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(sA + (sw ? tile_off_sw(r, k, 128) : tile_off(r, k, 16))) =
+            __float2bfloat16_rn(v);
     }
-    for (int e = tid; e < 32 * 16; e += 128) {
-        const int c = e / 16, k = e % 16;
+    for (int e = tid; e < 32 * K; e += 128) {
+        const int c = e / K, k = e % K;
         const float v = (float)((c % 5) - 2 + (k % 4));
-        *reinterpret_cast<__nv_bfloat16*>(sB + tile_off(c, k, 16)) = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(sB + (sw ? tile_off_sw(c, k, 32) : tile_off(c, k, 16))) =
+            __float2bfloat16_rn(v);
     }
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -167,8 +195,19 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restr
     const uint32_t tmem = tbase;
     const uint32_t lbo = variant == 0 ? 128u : 256u, sbo = variant == 0 ? 256u : 128u;
     if (tid == 0) {
-        mma_bf16(tmem, smem_desc(smem_u32(sA), lbo, sbo), smem_desc(smem_u32(sB), lbo, sbo),
-                 idesc_bf16(128, 32), 0u);
+        if (variant == 2) {          // four K steps of 16 inside the swizzle atom
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(tmem, smem_desc_sw128(smem_u32(sA) + 32u * kk),
+                         smem_desc_sw128(smem_u32(sB) + 32u * kk), idesc_bf16(128, 32), kk > 0 ? 1u : 0u);
+        } else if (variant == 3) {   // swizzled data read as unswizzled: must not match
+            for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(tmem, smem_desc(smem_u32(sA) + 32u * kk, 16u, 1024u),
+                         smem_desc(smem_u32(sB) + 32u * kk, 16u, 1024u), idesc_bf16(128, 32),
+                         kk > 0 ? 1u : 0u);
+        } else {
+            mma_bf16(tmem, smem_desc(smem_u32(sA), lbo, sbo), smem_desc(smem_u32(sB), lbo, sbo),
+                     idesc_bf16(128, 32), 0u);
+        }
         mma_commit(&bar);
     }
     const bool ok = __syncthreads_and(mbar_wait(&bar, 0)) != 0;
@@ -196,8 +235,9 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
     l = __float2bfloat16_rn(r2);
 }
 
-// Features of point i (packed xh, a at P[i*ps + dk]) written into the tiled layout:
-// role 0 = row operand, role 1 = column operand.  Rows beyond n are zero.
+// Features of point i (packed xh, a at P[i*ps + dk]) written into 128-row tiles in the
+// 128-byte swizzled layout (K slabs of 64): role 0 = row operand, role 1 = column
+// operand.  Rows beyond n and K columns beyond 6 dk + 6 are zero.
 __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, int ps, int Kp,
                               int role, long long nrows_pad, unsigned char* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,7 +247,7 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
     unsigned char* base = out + tile * (128LL * Kp * 2);
     const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
     auto put = [&](int k, __nv_bfloat16 v) {
-        *reinterpret_cast<__nv_bfloat16*>(base + tile_off(r, k, Kp)) = v;
+        *reinterpret_cast<__nv_bfloat16*>(base + tile_off_sw(r, k, 128)) = v;
     };
     if (i >= n) {
         for (int k = 0; k < Kp; ++k) put(k, zero);
@@ -240,14 +280,16 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
 // with cp.async.bulk, warp 1 lane 0 issues tcgen05.mma, warps 2..17 are the epilogue.
 // Hand-offs are mbarrier full/empty pairs only (no block-wide barrier in the loop):
 //   a_full / a_empty          the 256-row operand of the current work item
-//   s_full[s] / s_empty[s]    column tile stage s (empty needs the MMA commit and all
-//                             16 epilogue warps, because the epilogue reads V from it)
-//   t_full[b] / t_empty[b]    TMEM accumulator buffer b (2 x 256 columns)
+//   s_full[s] / s_empty[s]    column tile stage s (empty needs the MMA commit and the
+//                             8 epilogue warps of the tile's parity, which read V from it)
+//   t_full[b] / t_empty[b]    TMEM accumulator buffer b (2 x 256 columns), read by the
+//                             8 epilogue warps of parity b
 constexpr int TC_EPI_WARPS = 16;
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_BN = 128;        // columns per tile
 constexpr int TC_ROWS = 256;      // rows per work item
 constexpr int TC_NS = 4;          // pipeline stages for column tiles
+static_assert(TC_NS % 2 == 0, "a stage must always hold tiles of one parity");
 
 struct TcShared {
     uint64_t a_full, a_empty, s_full[TC_NS], s_empty[TC_NS], t_full[2], t_empty[2];
@@ -264,7 +306,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
           int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
           int tiles_per_split, double* __restrict__ part, int* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzle atoms need 1024-byte alignment; the launch adds 1 KB of slack for this
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t tileA = 128u * Kp * 2u;            // bytes of one 128-row feature tile
     unsigned char* sA = smem;                         // 2 tiles (256 rows)
     unsigned char* sB = smem + 2 * tileA;             // TC_NS column tiles
@@ -277,11 +321,11 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         mbar_init(&sh->a_empty, 1);
         for (int s = 0; s < TC_NS; ++s) {
             mbar_init(&sh->s_full[s], 1);
-            mbar_init(&sh->s_empty[s], 1 + TC_EPI_WARPS);
+            mbar_init(&sh->s_empty[s], 1 + TC_EPI_WARPS / 2);   // MMA + the 8 warps of its parity
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->t_full[b], 1);
-            mbar_init(&sh->t_empty[b], TC_EPI_WARPS);
+            mbar_init(&sh->t_empty[b], TC_EPI_WARPS / 2);
         }
         sh->abort = 0;
         fence_mbar_init();
@@ -327,7 +371,6 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(128, TC_BN);
-            const uint32_t sbo = (uint32_t)Kp * 16u;   // (Kp / 8) core matrices x 128 bytes
             const uint32_t a_addr = smem_u32(sA);
             uint32_t g = 0, ic = 0;
             for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
@@ -344,8 +387,10 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                     for (int h = 0; h < 2; ++h) {
                         const uint32_t d = tmem + (uint32_t)(b * 256 + h * 128);
                         for (int kk = 0; kk < Kp / 16; ++kk) {
-                            const uint64_t ad = smem_desc(a_addr + h * tileA + kk * 256u, 128u, sbo);
-                            const uint64_t bd = smem_desc(b_addr + kk * 256u, 128u, sbo);
+                            // slab kk / 4 (128 rows x 128 bytes), 32 bytes per K step inside it
+                            const uint32_t koff = (uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u;
+                            const uint64_t ad = smem_desc_sw128(a_addr + h * tileA + koff);
+                            const uint64_t bd = smem_desc_sw128(b_addr + koff);
                             mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
                         }
                     }
@@ -357,9 +402,13 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         }
     } else {
         // ---------------------------------------------------------- epilogue
+        // Warp e (0..15) reads TMEM lanes of its quarter (warp & 3), rows of its half of
+        // the 256-row item, all 128 columns, for the tiles of its parity only: on each
+        // SM sub-partition two warps work on even tiles and two on odd ones, so the TMEM
+        // load latency of one pair hides behind the exponentials of the other.
         const int e = warp - 2;                       // 0..15
         const int quarter = warp & 3;                 // TMEM lanes this warp may read
-        const int half = (e >> 2) & 1, cgrp = e >> 3;
+        const int half = (e >> 2) & 1, par = e >> 3;
         const int lrow = half * 128 + quarter * 32 + lane;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
@@ -377,21 +426,21 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             }
             bool ok = true;
             for (int t = t0; t < t1; ++t, ++g) {
-                const int s = g % TC_NS, b = g & 1;
+                if ((int)(g & 1u) != par) continue;
+                const int s = g % TC_NS, b = par;
                 ok = mbar_wait(&sh->t_full[b], (g >> 1) & 1u) && mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) { if (lane == 0) give_up(); break; }
                 tc_fence_after();
-                const float* v = sV + s * NRHS * TC_BN + cgrp * 64;
-                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) +
-                                    (uint32_t)(b * 256 + half * 128 + cgrp * 64);
-                // two 32-column halves: 32 live registers for the exponents instead of 64
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
+                const float* v = sV + s * NRHS * TC_BN;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + half * 128);
+                // 32-column chunks: 32 live registers for the exponents
+#pragma unroll 1
+                for (int hh = 0; hh < TC_BN / 32; ++hh) {
                     uint32_t r0[32];
                     tmem_ld32(tb + 32 * hh, r0);
                     tmem_wait_ld();
-                    if (hh == 1) {
+                    if (hh == TC_BN / 32 - 1) {
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
@@ -429,7 +478,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             if (row < nr) {
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q)
-                    part[(((size_t)sp * 2 + cgrp) * NRHS + q) * nr + row] = acc64[q];
+                    part[(((size_t)sp * 2 + par) * NRHS + q) * nr + row] = acc64[q];
             }
         }
     }
@@ -472,9 +521,11 @@ __global__ void __launch_bounds__(SK_THREADS, 1)
 k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB,
             const unsigned char* __restrict__ Om, int Kp, int n, int nab, int njc, int njc_alloc,
             int items, float* __restrict__ Y, int ldy, int* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // swizzle atoms need 1024-byte alignment; the launch adds 1 KB of slack for this
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t tileA = 128u * Kp * 2u;
-    const uint32_t tileB1 = (uint32_t)SK_JC * Kp * 2u;
+    const uint32_t tileB1 = (uint32_t)SK_JC * Kp * 2u;   // Kp / 64 slabs of 64 rows x 128 bytes
     unsigned char* sA = smem;
     unsigned char* sB1 = sA + tileA;                        // SK_NS x tileB1
     unsigned char* sB2 = sB1 + SK_NS * tileB1;              // SK_NS x SK_OMT
@@ -524,7 +575,11 @@ k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restric
                     const int s = g % SK_NS;
                     if (!mbar_wait(&sh->s_empty[s], ((g / SK_NS) & 1u) ^ 1u)) { give_up(); break; }
                     mbar_expect_tx(&sh->s_full[s], tileB1 + SK_OMT);
-                    bulk_g2s(sB1 + s * tileB1, FB + (size_t)jc * tileB1, tileB1, &sh->s_full[s]);
+                    // the 64-row chunk jc is half of 128-row tile jc / 2: one 8 KB piece per slab
+                    for (int sl = 0; sl < Kp / 64; ++sl)
+                        bulk_g2s(sB1 + s * tileB1 + sl * 8192u,
+                                 FB + (size_t)(jc >> 1) * tileA + (size_t)sl * 16384u + (size_t)(jc & 1) * 8192u,
+                                 8192u, &sh->s_full[s]);
                     bulk_g2s(sB2 + s * SK_OMT, Om + ((size_t)ab * njc_alloc + jc) * SK_OMT, SK_OMT,
                              &sh->s_full[s]);
                 }
@@ -533,7 +588,7 @@ k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restric
     } else if (warp == 1) {
         if (lane == 0) {   // ------------------------------------------------ MMA issuer
             const uint32_t id1 = idesc_bf16(128, SK_JC), id2 = idesc_bf16(128, SK_NB);
-            const uint32_t sbo1 = (uint32_t)Kp * 16u, sbo2 = SK_JC * 16u;
+            const uint32_t sbo2 = SK_JC * 16u;
             uint32_t g = 0, ic = 0;
             auto mma1 = [&](uint32_t gg) -> bool {      // exponents of chunk gg into S[gg & 1]
                 const int s = gg % SK_NS, b = gg & 1;
@@ -541,9 +596,11 @@ k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restric
                 if (!mbar_wait(&sh->x_empty[b], ((gg >> 1) & 1u) ^ 1u)) return false;
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(sB1 + s * tileB1);
-                for (int kk = 0; kk < Kp / 16; ++kk)
-                    mma_bf16(tmem + (uint32_t)(b * SK_JC), smem_desc(a_addr + kk * 256u, 128u, sbo1),
-                             smem_desc(b_addr + kk * 256u, 128u, sbo1), id1, kk > 0 ? 1u : 0u);
+                for (int kk = 0; kk < Kp / 16; ++kk)   // swizzled slabs: A 16 KB, B 8 KB apart
+                    mma_bf16(tmem + (uint32_t)(b * SK_JC),
+                             smem_desc_sw128(a_addr + (uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u),
+                             smem_desc_sw128(b_addr + (uint32_t)(kk >> 2) * 8192u + (uint32_t)(kk & 3) * 32u),
+                             id1, kk > 0 ? 1u : 0u);
                 mma_commit(&sh->x_full[b]);
                 return true;
             };
@@ -650,7 +707,7 @@ k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restric
 }
 
 // ------------------------------------------------------------------ host side
-int tc_feature_kp(int d) { return ((6 * kernel_dim(d) + 6) + 15) / 16 * 16; }
+int tc_feature_kp(int d) { return ((6 * kernel_dim(d) + 6) + 63) / 64 * 64; }
 
 // Y (n x ldy, FP32) = K Omega^T on tensor cores; Om from launch_omega_bf16_tiled with
 // njc_alloc = (padded n) / 64 chunks per projection block.
@@ -658,7 +715,7 @@ int launch_sketch_tc(krr_ctx* ctx, const unsigned char* FA, const unsigned char*
                      const void* Om, int l, int njc_alloc, float* Y, int ldy) {
     const int Kp = tc_feature_kp(d);
     const uint32_t tileA = 128u * Kp * 2u, tileB1 = (uint32_t)SK_JC * Kp * 2u;
-    const size_t smem = tileA + (size_t)SK_NS * (tileB1 + SK_OMT) + 2 * 128 * SK_JC * 2 + 256;
+    const size_t smem = tileA + (size_t)SK_NS * (tileB1 + SK_OMT) + 2 * 128 * SK_JC * 2 + 256 + 1024;
     KRR_RET(allow_max_dynamic_smem(ctx, (const void*)k_sketch_tc));
     int* err;
     KRR_RET(bufT(ctx, "tc_err", 1, &err));
@@ -716,11 +773,23 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
                                        sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
         const uint32_t tileA = 128u * Kp * 2u;
         const size_t smem = (2 + TC_NS) * (size_t)tileA + (size_t)TC_NS * chunk * TC_BN * 4 + 256;
-        const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
+        const size_t smem_launch = std::max<size_t>(smem + 1024, 120 * 1024);   // one CTA per SM (TMEM)
         KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
         const int nrb = (int)ceil_div(nr, TC_ROWS);
         const int ntiles = ncp / TC_BN;
-        int splits = choose_splits_public(nrb, ntiles, ctx->num_sms);
+        // column splits: the CTA with the most items sets the time, so minimise
+        // ceil(items / SMs) x (tiles per item + the per-item cost, about 8 tiles)
+        int splits = 1;
+        long long best = -1;
+        for (int sc = 1; sc <= std::min(64, ntiles); ++sc) {
+            const long long per = (ntiles + sc - 1) / sc;
+            const long long waves = ((long long)nrb * sc + ctx->num_sms - 1) / ctx->num_sms;
+            const long long cost = waves * (per + 8);
+            if (best < 0 || cost < best) {
+                best = cost;
+                splits = sc;
+            }
+        }
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
         const int items = nrb * splits;
@@ -744,7 +813,7 @@ using namespace krr;
 
 // Known-answer test of the tcgen05 descriptor encodings (host entry, see krr.h).
 extern "C" int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream_v) {
-    if (!mismatches || !max_err || variant < 0 || variant > 1) return KRR_E_INVAL;
+    if (!mismatches || !max_err || variant < 0 || variant > 3) return KRR_E_INVAL;
     cudaStream_t stream = (cudaStream_t)stream_v;
     float* out = nullptr;
     int* err = nullptr;
@@ -770,7 +839,7 @@ extern "C" int krr_tc_selftest(int variant, int* mismatches, float* max_err, voi
     for (int r = 0; r < 128; ++r)
         for (int c = 0; c < 32; ++c) {
             float ref = 0.f;
-            for (int k = 0; k < 16; ++k)
+            for (int k = 0; k < (variant >= 2 ? 64 : 16); ++k)
                 ref += (float)((r % 7) - 3 + (k % 3)) * (float)((c % 5) - 2 + (k % 4));
             const float d = std::fabs(h[r * 32 + c] - ref);
             mx = std::max(mx, d);

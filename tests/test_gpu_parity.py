@@ -112,6 +112,10 @@ def test_tc_descriptor_known_answer():
     assert bad == 0 and err == 0.0
     bad1, _ = api.tc_selftest(1)   # the swapped stride convention must be detected
     assert bad1 > 0
+    bad2, err2 = api.tc_selftest(2)   # 128-byte swizzled layout, K = 64 in four steps
+    assert bad2 == 0 and err2 == 0.0
+    bad3, _ = api.tc_selftest(3)   # the same data through an unswizzled descriptor
+    assert bad3 > 0
 
 
 @pytest.mark.parametrize("n,d,nrhs,beta", [(2000, 4, 1, 1e-2), (1, 3, 1, 0.5), (127, 2, 3, 0.0),
