@@ -30,10 +30,12 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// One bounded probe of the phase: the thread may suspend (up to the 1 ms hint) until the
+// phase completes instead of spinning, which keeps waiting warps off the issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000000;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -106,8 +108,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr)
         : "memory");
 }
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// Waits for this thread's TMEM loads; r is tied in as read-write so that no use of the
+// loaded registers can be scheduled above the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]),
+                   "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 // Shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restr
     if (ok) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
-        tmem_wait_ld();
+        tmem_wait_ld(r);
         const int row = warp * 32 + lane;
         for (int c = 0; c < 32; ++c) out[row * 32 + c] = __uint_as_float(r[c]);
     }
@@ -434,22 +446,13 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 tc_fence_after();
                 const float* v = sV + s * NRHS * TC_BN;
                 const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + half * 128);
-                // 32-column chunks: 32 live registers for the exponents
-#pragma unroll 1
-                for (int hh = 0; hh < TC_BN / 32; ++hh) {
-                    uint32_t r0[32];
-                    tmem_ld32(tb + 32 * hh, r0);
-                    tmem_wait_ld();
-                    if (hh == TC_BN / 32 - 1) {
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
-                    }
+                // one 32-column chunk of exponents r (columns 32 hh .. 32 hh + 31)
+                auto chunk = [&](const uint32_t (&r)[32], int hh) {
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
                         float ev[4];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) ev[u] = ex2f(__uint_as_float(r0[4 * j4 + u]));
+                        for (int u = 0; u < 4; ++u) ev[u] = ex2f(__uint_as_float(r[4 * j4 + u]));
 #pragma unroll
                         for (int q = 0; q < NRHS; ++q) {
                             const float4 vv =
@@ -459,6 +462,40 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                             acc[q][2 % NA] = fmaf(ev[2], vv.z, acc[q][2 % NA]);
                             acc[q][3 % NA] = fmaf(ev[3], vv.w, acc[q][3 % NA]);
                         }
+                    }
+                };
+                auto release = [&]() {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
+                };
+                static_assert(TC_BN == 128, "four 32-column chunks per tile");
+                if constexpr (NRHS <= 2) {
+                    // two register sets: the load of chunk c + 1 is in flight while chunk c
+                    // is exponentiated
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32(tb, ra);
+                    tmem_wait_ld(ra);
+                    tmem_ld32(tb + 32, rb);
+                    chunk(ra, 0);
+                    tmem_wait_ld(rb);
+                    tmem_ld32(tb + 64, ra);
+                    chunk(rb, 1);
+                    tmem_wait_ld(ra);
+                    tmem_ld32(tb + 96, rb);
+                    chunk(ra, 2);
+                    tmem_wait_ld(rb);
+                    release();
+                    chunk(rb, 3);
+                } else {
+                    // 32 live registers for the exponents
+#pragma unroll 1
+                    for (int hh = 0; hh < TC_BN / 32; ++hh) {
+                        uint32_t r0[32];
+                        tmem_ld32(tb + 32 * hh, r0);
+                        tmem_wait_ld(r0);
+                        if (hh == TC_BN / 32 - 1) release();
+                        chunk(r0, hh);
                     }
                 }
                 __syncwarp();
@@ -648,7 +685,7 @@ k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restric
                 tc_fence_after();
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * SK_JC + cg * 32), v);
-                tmem_wait_ld();
+                tmem_wait_ld(v);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->x_empty[b]);
@@ -679,7 +716,7 @@ k_sketch_tc(const unsigned char* __restrict__ FA, const unsigned char* __restric
             for (int u = 0; u < 4; ++u) {
                 uint32_t cv[32];
                 tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(256 + cg * 128 + 32 * u), cv);
-                tmem_wait_ld();
+                tmem_wait_ld(cv);
                 const int a0 = ab * SK_NB + cg * 128 + 32 * u;
                 if (row < n) {
                     float4* dst = reinterpret_cast<float4*>(Y + (size_t)row * ldy + a0);
