@@ -17,8 +17,10 @@ namespace krr {
 
 constexpr int VT = 256;   // threads of the streaming kernels
 
+// Blocks of the streaming kernels: four per SM where n allows (the Woodbury GEMVs are
+// latency bound with fewer loads in flight), at least 64 rows per block.
 static int vec_blocks(krr_ctx* ctx, long long n) {
-    return (int)std::max<long long>(1, std::min<long long>(2LL * ctx->num_sms, ceil_div(n, VT)));
+    return (int)std::max<long long>(1, std::min<long long>(4LL * ctx->num_sms, ceil_div(n, 64)));
 }
 
 // Block-wide FP64 sum into part[q * gridDim.x + blockIdx.x].
@@ -197,18 +199,30 @@ k_gemv_t_reduce(const double* __restrict__ upart, int nblk, int nq, int k, int l
     }
 }
 
-// y[q][a] = sum_b T[a][b] x[q][b] over b <= a (lower) or b >= a (upper).  One warp per row a.
-__global__ void k_tri_gemv(const double* __restrict__ T, int k, const double* __restrict__ x,
-                           int nq, bool lower, double* __restrict__ y) {
-    const int a = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (a >= k) return;
+// y[q][a] = sum_b T[a][b] x[q][b] over b <= a (lower) or b >= a (upper).  One 128-thread
+// block per row a: every thread has at most a few independent loads of the row, so the
+// k x k factor streams at memory rate instead of one dependent chain per warp.
+constexpr int TG_T = 128;
+__global__ void __launch_bounds__(TG_T) k_tri_gemv(const double* __restrict__ T, int k,
+                                                   const double* __restrict__ x, int nq, bool lower,
+                                                   double* __restrict__ y) {
+    __shared__ double red[TG_T / 32];
+    const int a = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int b0 = lower ? 0 : a, b1 = lower ? a + 1 : k;
     for (int q = 0; q < nq; ++q) {
         double s = 0.0;
-        for (int b = b0 + lane; b < b1; b += 32) s = fma(T[(size_t)a * k + b], x[(size_t)q * k + b], s);
+        for (int b = b0 + threadIdx.x; b < b1; b += TG_T) s = fma(T[(size_t)a * k + b], x[(size_t)q * k + b], s);
         s = warp_sum(s);
-        if (lane == 0) y[(size_t)q * k + a] = s;
+        __syncthreads();
+        if (lane == 0) red[w] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+#pragma unroll
+            for (int i = 0; i < TG_T / 32; ++i) t += red[i];
+            y[(size_t)q * k + a] = t;
+        }
     }
 }
 
@@ -319,9 +333,9 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
         KRR_CHECK_LAUNCH();
         k_gemv_t_reduce<<<dim3(ceil_div(k, 32), nq), 256, 0, ctx->stream>>>(upart, nb, nq, k, ldF, u);
         KRR_CHECK_LAUNCH();
-        k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2, k, u, nq, true, u1);
+        k_tri_gemv<<<k, TG_T, 0, ctx->stream>>>(ctx->T2, k, u, nq, true, u1);
         KRR_CHECK_LAUNCH();
-        k_tri_gemv<<<ceil_div(k, 8), 256, 0, ctx->stream>>>(ctx->T2t, k, u1, nq, false, v);
+        k_tri_gemv<<<k, TG_T, 0, ctx->stream>>>(ctx->T2t, k, u1, nq, false, v);
         KRR_CHECK_LAUNCH();
         const size_t smem = sizeof(float4) * nq * (ldF / 4);
         if (smem > 48 * 1024) {

@@ -97,8 +97,11 @@ def test_autograd_function_matches_grad():
     ctx.build(X, p.sigma, p.beta, p.k, seed=3)
     loss, ds, db, dy = ctx.grad(y.detach(), Xv, yv, tol=1e-9)
     assert float(L.detach()) == pytest.approx(loss, rel=1e-9)
-    assert float(ls.grad) == pytest.approx(ds, rel=1e-6)
-    assert float(lb.grad) == pytest.approx(db, rel=1e-6)
+    # two builds, each solved to a 1e-9 residual: the adjoint carries that residual times
+    # the condition of K + beta I into the gradient, about 1e-6 here (the oracle and
+    # finite-difference tests hold the gradient itself to 1e-4)
+    assert float(ls.grad) == pytest.approx(ds, rel=1e-5)
+    assert float(lb.grad) == pytest.approx(db, rel=1e-5)
     # two separate builds (sigma = exp(log sigma) differs in the last bit), each solved to 1e-9
     gy, ref = y.grad.double().cpu().numpy(), dy.cpu().numpy()
-    assert np.linalg.norm(gy - ref) / np.linalg.norm(ref) <= 1e-6
+    assert np.linalg.norm(gy - ref) / np.linalg.norm(ref) <= 1e-5
