@@ -396,6 +396,54 @@ def run_batched(args):
     return 0
 
 
+# ------------------------------------------------------------------ gradient workload
+def run_gradient(args):
+    """Held-out-MSE gradient (krr_grad: solve, adjoint solve, derivative products) on the
+    200000 + 20000 point workload, d = 10; checked against central differences of the
+    loss in log sigma and log beta.  Reported beside the main line, not as the headline."""
+    import torch
+    from paper_1905_10587_gb300.build import build
+    build()
+    from paper_1905_10587_gb300 import api
+    import synth
+    p = synth.gradient()
+    X = torch.from_numpy(p.X).cuda()
+    y = torch.from_numpy(p.Y[:, 0].copy()).cuda()
+    Xv = torch.from_numpy(p.Xval).cuda()
+    yv = torch.from_numpy(p.yval).cuda()
+    tol = 1e-7
+
+    def grad_at(log_sigma, log_beta):
+        ctx = api.KRR(precision=args.precision)
+        ctx.build(X, float(np.exp(log_sigma)), float(np.exp(log_beta)), p.k, seed=1)
+        out = ctx.grad(y, Xv, yv, tol=tol)
+        ctx.close()
+        return out
+
+    ls0, lb0 = float(np.log(p.sigma)), float(np.log(p.beta))
+    grad_at(ls0, lb0)                                  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss, ds, db, dy = grad_at(ls0, lb0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h = 1e-3
+    fd_s = (grad_at(ls0 + h, lb0)[0] - grad_at(ls0 - h, lb0)[0]) / (2 * h)
+    fd_b = (grad_at(ls0, lb0 + h)[0] - grad_at(ls0, lb0 - h)[0]) / (2 * h)
+    print(json.dumps({"metric": "held-out MSE gradient seconds (build + solve + adjoint solve + "
+                                "derivative products)", "value": dt, "unit": "s",
+                      "higher_is_better": False, "n_gpus": 1,
+                      "config": {"workload": f"n={p.n} train + {p.Xval.shape[0]} held-out, d={p.d}, "
+                                             f"X ~ N(0, I), sigma={p.sigma:g}, beta={p.beta:g}, k={p.k}, "
+                                             f"solve tol {tol:g}", "precision": args.precision},
+                      "loss": loss, "dlogsigma": ds, "dlogbeta": db,
+                      "fd_dlogsigma": fd_s, "fd_dlogbeta": fd_b,
+                      "rel_diff_dlogsigma": abs(ds - fd_s) / max(abs(fd_s), 1e-300),
+                      "rel_diff_dlogbeta": abs(db - fd_b) / max(abs(fd_b), 1e-300),
+                      "fd_step": h, "dy_norm": float(dy.norm().item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,13 +457,15 @@ def main():
     ap.add_argument("--no-other-form", action="store_true")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="kernel product: 0 FP32 tiles, 1 tensor-core tiles (default)")
-    ap.add_argument("--workload", default="mixture", choices=["mixture", "batched"])
+    ap.add_argument("--workload", default="mixture", choices=["mixture", "batched", "gradient"])
     ap.add_argument("--workers", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "gradient":
+        return run_gradient(args)
     return run_gpu(args)
 
 

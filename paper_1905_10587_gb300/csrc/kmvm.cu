@@ -232,6 +232,172 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
     }
 }
 
+// ------------------------------------------------------------------ paired-row FP32 product
+// The same products as k_kmvm for an even number of rows per thread, two rows at a time
+// on the paired FP32 instructions (fma/add/sub/mul.rn.f32x2): each instruction does the
+// two rows' operations with the same rounding as two scalar ones, so the result equals
+// k_kmvm's bit for bit while the exponent costs half the issue slots.  The column tile
+// is staged with every coordinate duplicated ((x, x) per 64-bit word) so one shared load
+// feeds both halves.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int D, int NRHS, int R, bool RAW>
+__global__ void __launch_bounds__(KM_THREADS, 4)
+k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
+        const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc,
+        float* __restrict__ Q, int ldq, double* __restrict__ part) {
+    static_assert(R % 2 == 0, "rows in pairs");
+    constexpr int PS = (D + 1 + 3) / 4 * 4;
+    constexpr int PS4 = PS / 4;
+    constexpr int PH = PS / 2;                     // 128-bit words per column (2 duplicated coords)
+    constexpr int RP = R / 2;
+    __shared__ ulonglong2 sP2[KM_BN * PH];
+    __shared__ __align__(16) float sV[KM_BN * NRHS];
+
+    const int tid = threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * (KM_THREADS * R);
+
+    unsigned long long xi[RP][D];
+    unsigned long long ai[RP];
+    unsigned long long acc[RP][NRHS];   // one column tile, FP32 pairs
+    double acc64[R][NRHS];              // tiles folded in FP64
+#pragma unroll
+    for (int pr = 0; pr < RP; ++pr) {
+        float xv[2][D], av[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long i = row0 + (2 * pr + h) * KM_THREADS + tid;
+            const bool ok = i < nr;
+#pragma unroll
+            for (int c = 0; c < D; ++c) xv[h][c] = ok ? (RAW ? 1.f : 2.f) * Pr[i * PS + c] : 0.f;
+            av[h] = (ok && !RAW) ? Pr[i * PS + D] : 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) xi[pr][c] = f2_pack(xv[0][c], xv[1][c]);
+        ai[pr] = f2_pack(av[0], av[1]);
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) acc[pr][q] = 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int q = 0; q < NRHS; ++q) acc64[r][q] = 0.0;
+    const unsigned long long nsc2 = f2_pack(nsc, nsc);
+
+    const int ntiles = (nc + KM_BN - 1) / KM_BN;
+    const int t0 = blockIdx.y * tiles_per_split;
+    const int t1 = min(t0 + tiles_per_split, ntiles);
+    const float4* Pc4 = reinterpret_cast<const float4*>(Pc);
+
+    for (int t = t0; t < t1; ++t) {
+        const int c0 = t * KM_BN;
+        for (int e = tid; e < KM_BN * PS4; e += KM_THREADS) {
+            const int j = e / PS4, w = e - j * PS4;
+            const float4 v = (c0 + j < nc) ? Pc4[(size_t)(c0 + j) * PS4 + w] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sP2[j * PH + 2 * w] = make_ulonglong2(f2_pack(v.x, v.x), f2_pack(v.y, v.y));
+            sP2[j * PH + 2 * w + 1] = make_ulonglong2(f2_pack(v.z, v.z), f2_pack(v.w, v.w));
+        }
+        for (int e = tid; e < KM_BN * NRHS; e += KM_THREADS) {
+            const int q = e / KM_BN, j = e - q * KM_BN;
+            sV[j * NRHS + q] = (c0 + j < nc) ? V[(size_t)q * ldv + c0 + j] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int j = 0; j < KM_BN; ++j) {
+            unsigned long long xj[PS];
+#pragma unroll
+            for (int w = 0; w < PH; ++w) {
+                const ulonglong2 v = sP2[j * PH + w];
+                xj[2 * w] = v.x;
+                xj[2 * w + 1] = v.y;
+            }
+            unsigned long long vj[NRHS];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) {
+                const float v = sV[j * NRHS + q];
+                vj[q] = f2_pack(v, v);
+            }
+#pragma unroll
+            for (int pr = 0; pr < RP; ++pr) {
+                unsigned long long tt;
+                if constexpr (RAW) {
+                    unsigned long long ss = 0ull;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        const unsigned long long df = f2_sub(xi[pr][c], xj[c]);
+                        ss = f2_fma(df, df, ss);
+                    }
+                    tt = f2_mul(ss, nsc2);
+                } else {
+                    tt = f2_add(ai[pr], xj[D]);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) tt = f2_fma(xi[pr][c], xj[c], tt);
+                }
+                float t0f, t1f;
+                f2_unpack(tt, t0f, t1f);
+                const unsigned long long e = f2_pack(ex2f(t0f), ex2f(t1f));
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q) acc[pr][q] = f2_fma(e, vj[q], acc[pr][q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int pr = 0; pr < RP; ++pr)
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) {
+                float lo, hi;
+                f2_unpack(acc[pr][q], lo, hi);
+                acc64[2 * pr][q] += (double)lo;
+                acc64[2 * pr + 1][q] += (double)hi;
+                acc[pr][q] = 0ull;
+            }
+    }
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const long long i = row0 + r * KM_THREADS + tid;
+        if (i >= nr) continue;
+        if (part == nullptr) {
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+                Q[(size_t)q * ldq + i] =
+                    (float)(acc64[r][q] + (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
+        } else {
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q)
+                part[((size_t)blockIdx.y * NRHS + q) * nr + i] = acc64[r][q];
+        }
+    }
+}
+
 __global__ void k_kmvm_reduce(const double* __restrict__ part, int splits, int nr, int nrhs,
                               const float* __restrict__ V, int ldv, float beta,
                               float* __restrict__ Q, int ldq) {
@@ -274,8 +440,12 @@ typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int,
 
 template <int D, int NRHS>
 static kmvm_fn pick2(bool raw) {
-    return raw ? &k_kmvm<D, NRHS, kmvm_rows<D, NRHS>(), true>
-               : &k_kmvm<D, NRHS, kmvm_rows<D, NRHS>(), false>;
+    constexpr int R = kmvm_rows<D, NRHS>();
+    if constexpr (R % 2 == 0 && D <= 24) {
+        return raw ? &k_kmvm2<D, NRHS, R, true> : &k_kmvm2<D, NRHS, R, false>;
+    } else {
+        return raw ? &k_kmvm<D, NRHS, R, true> : &k_kmvm<D, NRHS, R, false>;
+    }
 }
 
 template <int D>
