@@ -411,7 +411,7 @@ def run_gradient(args):
     y = torch.from_numpy(p.Y[:, 0].copy()).cuda()
     Xv = torch.from_numpy(p.Xval).cuda()
     yv = torch.from_numpy(p.yval).cuda()
-    tol = 1e-7
+    tol = 1e-6
 
     def grad_at(log_sigma, log_beta):
         ctx = api.KRR(precision=args.precision)
