@@ -143,7 +143,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     p = _workload(args.n, 0)
-    mvm_guess = 240   # products of a typical solve of this workload on the GPU path
+    mvm_guess = 780   # products of a solve of this workload on the GPU path (tensor-core form)
     vals = []
     for s in range(args.warmup + args.steps):
         r = oracle_sample(p, mvm_guess, budget_s=min(20.0, 120.0 / max(1, args.warmup + args.steps)))
@@ -414,7 +414,7 @@ def run_gradient(args):
     tol = 1e-6
 
     def grad_at(log_sigma, log_beta):
-        ctx = api.KRR(precision=args.precision)
+        ctx = api.KRR(precision=args.precision, max_iter=20000)
         ctx.build(X, float(np.exp(log_sigma)), float(np.exp(log_beta)), p.k, seed=1)
         out = ctx.grad(y, Xv, yv, tol=tol)
         ctx.close()
