@@ -161,6 +161,13 @@ def run_reference(args):
     return 0
 
 
+# DRAM bytes of one product launch (dram__bytes_read.sum + dram__bytes_write.sum from one
+# ncu capture of the current kernel on this workload): (form, n, d) -> bytes.  For the
+# tensor-core form this equals its algorithmic bytes (both feature sets, 2 n Kp bytes each,
+# plus V); the column features' re-reads are L2 hits.
+MEASURED_TRAFFIC = {(1, 100000, 8): 26_060_000}
+
+
 # ------------------------------------------------------------------ roofline of the product
 def roofline(p, kms, kcnt, clocks, precision, sms):
     """ALU roofline of the kernel product (the dominant kernel of the solve).
@@ -184,7 +191,9 @@ def roofline(p, kms, kcnt, clocks, precision, sms):
             else "k_kmvm (tiled FP32 kernel product), (K + beta I) p")
     return {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
             "peak": peak_pairs / 1e9, "unit": "Gpair/s",
-            "frac": (achieved / peak_pairs) if achieved else None, "traffic": None,
+            "frac": (achieved / peak_pairs) if achieved else None,
+            "traffic": MEASURED_TRAFFIC.get((precision, p.n, p.d)),
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
             "kernel": name,
             "peak_basis": (f"derived from unit counts x max clock ({sm_max / 1e6:.0f} MHz): "
                            f"{sms} SMs x 128 FP32 lanes / {fma_per_pair} FMA-pipe ops per pair, "
