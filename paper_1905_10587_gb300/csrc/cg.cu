@@ -177,24 +177,26 @@ k_gemv_t(const float* __restrict__ F, long long n, int ldF, const float* __restr
     }
 }
 
-// u[q][a] = sum_blk upart (FP64), a < k.  A CTA covers 32 columns; its 8 warps split the
-// partials and combine them through shared memory (coalesced, many loads in flight).
+// u[q][a] = sum_blk upart (FP64), a < k.  A CTA covers 8 columns with 32 groups of 8
+// threads: each group sums every 32nd partial (8 consecutive columns = one 64-byte
+// segment per load), and the groups combine through shared memory.  k / 8 CTAs keep
+// enough loads in flight for the 4 x SMs partials of the F^T r pass.
 __global__ void __launch_bounds__(256)
 k_gemv_t_reduce(const double* __restrict__ upart, int nblk, int nq, int k, int ldF,
                 double* __restrict__ u) {
-    __shared__ double red[8][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int a = blockIdx.x * 32 + lane;
+    __shared__ double red[32][9];
+    const int c = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int a = blockIdx.x * 8 + c;
     const int q = blockIdx.y;
     double s = 0.0;
     if (a < k)
-        for (int b = w; b < nblk; b += 8) s += upart[((size_t)b * nq + q) * ldF + a];
-    red[w][lane] = s;
+        for (int b = g; b < nblk; b += 32) s += upart[((size_t)b * nq + q) * ldF + a];
+    red[g][c] = s;
     __syncthreads();
-    if (w == 0 && a < k) {
+    if (threadIdx.x < 8 && a < k) {
         double t = 0.0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t += red[i][lane];
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) t += red[i][c];
         u[(size_t)q * k + a] = t;
     }
 }
@@ -331,7 +333,7 @@ int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, doubl
         float* Zq = Z + (size_t)q0 * n;
         gt<<<nb, VT, 0, ctx->stream>>>(ctx->F, n, ldF, Rq, n, rows_per, upart);
         KRR_CHECK_LAUNCH();
-        k_gemv_t_reduce<<<dim3(ceil_div(k, 32), nq), 256, 0, ctx->stream>>>(upart, nb, nq, k, ldF, u);
+        k_gemv_t_reduce<<<dim3(ceil_div(k, 8), nq), 256, 0, ctx->stream>>>(upart, nb, nq, k, ldF, u);
         KRR_CHECK_LAUNCH();
         k_tri_gemv<<<k, TG_T, 0, ctx->stream>>>(ctx->T2, k, u, nq, true, u1);
         KRR_CHECK_LAUNCH();
