@@ -218,8 +218,9 @@ int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out);
  * FP32 with reliable updates: its recursive residual is replaced by the true one
  * (and its iterate folded into the FP64 alpha) each time it drops by
  * opts.inner_tol.  X must be the pointer given to the build.  alpha: n x nrhs FP64.
- * info (host) may be NULL.  Returns KRR_E_NOCONV (alpha still written) if
- * the limits are hit first. */
+ * info (host) may be NULL.  Returns KRR_E_NOCONV if the limits are hit first;
+ * alpha then holds, per column, the iterate with the smallest true residual seen
+ * (info->rel_residual reports that residual). */
 int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol,
               double* alpha, krr_solve_info* info);
 

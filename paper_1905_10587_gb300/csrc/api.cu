@@ -671,6 +671,11 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     const double delta2 = ctx->opts.inner_tol * ctx->opts.inner_tol;
     std::vector<double> rtrue(nrhs);
     std::vector<int> act(nrhs);
+    // per column, the alpha with the smallest true residual so far: a solve that ends
+    // without reaching tol returns that one, never a worse later iterate
+    double* abest;
+    KRR_RET(bufT(ctx, "sv_abest", (size_t)tot, &abest));
+    std::vector<double> best_rel(nrhs, HUGE_VAL);
     auto true_residual = [&](bool first) -> int {
         if (first) {
             KRR_RET(launch_convert_up(ctx, Y, r64, tot));
@@ -702,6 +707,12 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             worst = std::max(worst, rel);
         }
         if (inf.sweeps < 8) inf.sweep_residual[inf.sweeps] = worst;
+        for (int c = 0; c < nrhs; ++c)
+            if (inf.rel_residual[c] < best_rel[c]) {
+                best_rel[c] = inf.rel_residual[c];
+                KRR_TRY_CUDA(cudaMemcpyAsync(abest + (size_t)c * n, alpha + (size_t)c * n, sizeof(double) * n,
+                                             cudaMemcpyDeviceToDevice, ctx->stream));
+            }
         KRR_RET(launch_convert(ctx, r64, r, tot));
         return KRR_OK;
     };
@@ -835,9 +846,14 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             }
         }
         inf.iters = it;
-        if (status != KRR_OK && since > 0) {
-            // fold the last partial correction so that alpha is the best iterate
-            KRR_RET(launch_accumulate(ctx, x, alpha, tot));
+        if (status != KRR_OK) {
+            // the last partial correction (if any) is unverified: return each column's best
+            for (int c = 0; c < nrhs; ++c)
+                if (since > 0 || inf.rel_residual[c] > best_rel[c]) {
+                    KRR_TRY_CUDA(cudaMemcpyAsync(alpha + (size_t)c * n, abest + (size_t)c * n,
+                                                 sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+                    inf.rel_residual[c] = best_rel[c];
+                }
         }
     }
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));

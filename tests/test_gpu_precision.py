@@ -136,3 +136,19 @@ def test_wide_cube_products_full_size_sampled(prec):
     rows = np.random.Generator(np.random.PCG64(21)).choice(p.n, 64, replace=False)
     ref = O.kmvm(p.X, p.Y.astype(np.float64), p.sigma, p.beta, rows=rows)
     assert _relcols(Q[rows], ref).max() <= 1e-5
+
+
+def test_unconverged_solve_returns_its_best_iterate():
+    # a solve cut off by max_iter reports KRR_E_NOCONV; alpha is the iterate with the
+    # smallest verified residual, and the reported residual is that alpha's
+    from paper_1905_10587_gb300 import _lib
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.small()
+    ctx = KRR(max_iter=7)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=3)
+    a, info = ctx.solve(_t(p.Y), tol=1e-12, allow_noconv=True)
+    assert info["status"] == _lib.KRR_E_NOCONV
+    a = a.cpu().numpy()
+    res = np.linalg.norm(O.residual(p.X, a, p.Y, p.sigma, p.beta)) / np.linalg.norm(p.Y)
+    assert res <= 1.0
+    assert res == pytest.approx(info["rel_residual"][0], rel=1e-6, abs=1e-12)
