@@ -33,6 +33,8 @@ Readings where the paper is silent or garbled (all listed in the design notes):
   * The random test matrix is drawn with Philox4x32-10 (Salmon et al., SC'11)
     and Box-Muller, defined in ``omega`` below; the CUDA path implements the
     same published generator independently.
+  * Algorithm 2's "set R of r values chosen randomly" is drawn with replacement
+    (independent uniform indices, ``sparse_draw``); the paper gives no r.
 """
 from __future__ import annotations
 
@@ -241,6 +243,48 @@ def anchor_selection(X: np.ndarray, sigma: float, k: int, l: int, seed: int):
     Om = omega(seed, l, X.shape[0])
     Y = sketch(X, sigma, Om)
     S, _ = qrcp(Y.T, k)
+    return S
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 2 (SparseAnchorSelection)
+# ----------------------------------------------------------------------------
+SPARSE_TAG = 0x53505253   # third Philox counter word of the sparse draws ("SPRS")
+
+
+def sparse_draw(seed: int, l: int, r: int, n: int):
+    """Algorithm 2, steps 3-4: for each projection i a set R of r row indices and a
+    Rademacher vector v.
+
+    Entry (i, m) uses Philox4x32-10 with counter (i, m, SPARSE_TAG, 0) and key
+    (seed mod 2^32, seed div 2^32); with r0, r1 the first two output words the index
+    is floor(r0 n / 2^32) and the sign is +1 if the top bit of r1 is clear, else -1.
+    Indices are drawn independently (with replacement): for r << n this is a set
+    except for rare repeats, which then count twice.  Returns (R, v), both l x r.
+    """
+    i = np.repeat(np.arange(l, dtype=np.uint64), r)
+    m = np.tile(np.arange(r, dtype=np.uint64), l)
+    k0, k1 = seed & _MASK, (seed >> 32) & _MASK
+    r0, r1, _, _ = philox4x32_10(i, m, np.full(i.shape, SPARSE_TAG, np.uint64),
+                                 np.zeros(i.shape, np.uint64), k0, k1)
+    R = ((r0 * np.uint64(n)) >> np.uint64(32)).astype(np.int64).reshape(l, r)
+    v = np.where((r1 >> np.uint64(31)) == 0, 1.0, -1.0).reshape(l, r)
+    return R, v
+
+
+def sparse_sketch(X: np.ndarray, sigma: float, R: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Algorithm 2, steps 5-6: Y(:, i) = K(X, X_R) v for each projection i (n x l)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.empty((X.shape[0], R.shape[0]))
+    for i in range(R.shape[0]):
+        Y[:, i] = kmvm_rect(X, X[R[i]], v[i], sigma)
+    return Y
+
+
+def sparse_anchor_selection(X: np.ndarray, sigma: float, k: int, l: int, r: int, seed: int):
+    """Algorithm 2: sparse sketch, pivoted QR on Y^T, S = first k pivots."""
+    R, v = sparse_draw(seed, l, r, X.shape[0])
+    S, _ = qrcp(sparse_sketch(X, sigma, R, v).T, k)
     return S
 
 

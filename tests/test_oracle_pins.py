@@ -312,3 +312,71 @@ def test_iteration_estimates_are_consistent():
     e2 = O.iters_preconditioned(1.0, 1e4, 1e-2, 1e-6)
     assert e2 == pytest.approx(e1, rel=0.05)
     assert O.iters_preconditioned(1.0, 1e-3, 1e-2, 1e-6) < e2
+
+
+# ------------------------------------------------ Algorithm 2 (sparse anchors)
+def test_sparse_draw_is_uniform_rademacher_and_deterministic():
+    n = 1000
+    R, v = O.sparse_draw(77, 400, 50, n)
+    assert R.shape == (400, 50) and v.shape == (400, 50)
+    assert R.min() >= 0 and R.max() < n
+    assert set(np.unique(v)) == {-1.0, 1.0}
+    # indices uniform on {0..n-1}: chi-square over 10 equal bins, signs fair
+    counts = np.bincount(R.ravel() * 10 // n, minlength=10)
+    assert st.chisquare(counts).pvalue > 1e-3
+    assert abs(v.mean()) < 0.02
+    R2, v2 = O.sparse_draw(77, 400, 50, n)
+    assert np.array_equal(R, R2) and np.array_equal(v, v2)
+    assert not np.array_equal(O.sparse_draw(78, 4, 5, n)[0], O.sparse_draw(77, 4, 5, n)[0])
+
+
+def test_sparse_draw_word_layout():
+    # entry (i, m) = (2, 3): Philox counter (2, 3, tag, 0), key (seed, 0); index is the
+    # high 32 bits of r0 * n, sign from the top bit of r1
+    w = O.philox4x32_10(2, 3, O.SPARSE_TAG, 0, 5, 0)
+    R, v = O.sparse_draw(5, 4, 6, 999)
+    assert R[2, 3] == (int(w[0]) * 999) // 2 ** 32
+    assert v[2, 3] == (1.0 if int(w[1]) < 2 ** 31 else -1.0)
+
+
+def test_sparse_sketch_brute_force():
+    X = _pts(23, 3, 31, scale=2.0)
+    R, v = O.sparse_draw(9, 6, 4, 23)
+    sigma = 0.7
+    Y = O.sparse_sketch(X, sigma, R, v)
+    for i in range(6):
+        for j in range(23):
+            s = 0.0
+            for m in range(4):
+                d2 = sum((X[j, c] - X[R[i, m], c]) ** 2 for c in range(3))
+                s += math.exp(-d2 / (2 * sigma * sigma)) * v[i, m]
+            assert Y[j, i] == pytest.approx(s, rel=1e-12, abs=1e-15)
+
+
+def test_sparse_anchors_pick_one_point_per_cluster():
+    # k distinct points, each repeated: K has rank k, every projection column lies in its
+    # span, and the pivoted QR must return k points from k different clusters
+    rng = np.random.Generator(np.random.PCG64(3))
+    centres = rng.uniform(0, 6, size=(5, 2))
+    X = np.repeat(centres, 30, axis=0)
+    S = O.sparse_anchor_selection(X, 1.0, 5, 12, 4, seed=11)
+    groups = S // 30
+    assert len(set(groups.tolist())) == 5
+
+
+def test_sparse_anchors_are_comparable_to_gaussian_ones():
+    # same k: the Nystrom error of the sparse ID stays within a small factor of Algorithm 1's
+    # and well below that of anchors drawn uniformly at random
+    X = _pts(600, 2, 5, scale=3.0)
+    sigma, k = 0.5, 40
+    K = O.kernel_matrix(X, X, sigma)
+
+    def err(S):
+        C = K[:, S]
+        return np.linalg.norm(K - C @ np.linalg.pinv(K[np.ix_(S, S)]) @ C.T, 2)
+
+    e_sparse = err(O.sparse_anchor_selection(X, sigma, k, k + 5, 8, seed=2))
+    e_gauss = err(O.anchor_selection(X, sigma, k, k + 5, seed=2))
+    e_random = err(np.random.Generator(np.random.PCG64(0)).choice(600, k, replace=False))
+    assert e_sparse <= 2 * e_gauss          # 1.69 vs 1.85 here
+    assert e_sparse <= 0.5 * e_random       # uniformly random anchors: 7.1
