@@ -75,7 +75,9 @@ typedef struct krr_opts {
     int    escalate;      /* 1 (default): when PCG meets non-positive curvature, or the
                              true residual stops falling, on precision 0 or 1, switch the
                              product to precision 2 and restart from the current alpha  */
-    int    reserved[3];
+    int    sparse_r;      /* 0 (default): Gaussian sketch (Algorithm 1); r > 0: sparse
+                             sketch of Algorithm 2 with r nonzeros per projection (<= 1024) */
+    int    reserved[2];
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -186,6 +188,20 @@ int krr_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, float* 
  * otherwise in FP32 tiles. */
 int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, int l,
                unsigned long long seed, float* Y);
+
+/* Algorithm 2, steps 3-4 (Section 3, SparseAnchorSelection): for each of the l
+ * projections, r row indices in [0, n) and r Rademacher signs.  Entry (i, m) comes from
+ * Philox4x32-10 with counter (i, m, 0x53505253, 0) and key (seed lo, seed hi): the index
+ * is the high word of r0 * n, the sign is -1 when the top bit of r1 is set.  Indices are
+ * drawn independently (with replacement).  R (int) and S (float): l x r, row-major, device. */
+int krr_sparse_draw(krr_ctx* ctx, unsigned long long seed, int l, int r, long long n, int* R, float* S);
+
+/* Algorithm 2, steps 5-6: Y(:, i) = K(X, X_R) v for the draws of krr_sparse_draw, FP32
+ * tiles from the packed points (as krr_sketch).  Y: n x l row-major (Y[j * l + i]),
+ * device.  The context's build state is reset.  Fails with KRR_E_INVAL when r
+ * points of dimension d do not fit 40 KB of shared memory. */
+int krr_sparse_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, int l, int r,
+                      unsigned long long seed, float* Y);
 
 /* Column-pivoted QR pivot selection of Algorithm 1 steps 3-4 on Y^T (Y is n x l
  * row-major, so the columns of Y^T are the rows of Y): returns the first k pivots

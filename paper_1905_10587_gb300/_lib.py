@@ -26,7 +26,7 @@ class KrrOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("refine_max", C.c_int), ("oversample", C.c_int),
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
-                ("escalate", C.c_int), ("reserved", C.c_int * 3)]
+                ("escalate", C.c_int), ("sparse_r", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class KrrSolveInfo(C.Structure):
@@ -61,6 +61,8 @@ SIGNATURES = {
     "krr_omega": (_i, [_vp, _ull, _i, _ll, _vp]),
     "krr_sketch": (_i, [_vp, _vp, _ll, _i, _d, _i, _ull, _vp]),
     "krr_qrcp": (_i, [_vp, _vp, _ll, _i, _i, _vp, _vp]),
+    "krr_sparse_draw": (_i, [_vp, _ull, _i, _i, _ll, _vp, _vp]),
+    "krr_sparse_sketch": (_i, [_vp, _vp, _ll, _i, _d, _i, _i, _ull, _vp]),
     "krr_build_precond": (_i, [_vp, _vp, _ll, _i, _d, _d, _i, _ull]),
     "krr_build_precond_anchors": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _i]),
     "krr_get_anchors": (_i, [_vp, _vp, C.POINTER(_i)]),

@@ -150,6 +150,23 @@ class KRR:
         self._X = None
         return Y
 
+    def sparse_draw(self, seed: int, l: int, r: int, n: int, device=None):
+        """Algorithm 2 steps 3-4: row indices R (l x r, int32) and Rademacher signs (l x r)."""
+        dev = device or torch.device("cuda")
+        R = torch.empty((l, r), device=dev, dtype=torch.int32)
+        S = torch.empty((l, r), device=dev, dtype=torch.float32)
+        self._check(self.lib.krr_sparse_draw(self.h, seed, l, r, n, _ptr(R), _ptr(S)))
+        return R, S
+
+    def sparse_sketch(self, X, sigma: float, l: int, r: int, seed: int) -> torch.Tensor:
+        """Y (n x l) of Algorithm 2 steps 5-6: column i = K(X, X_R) v for the i-th draw."""
+        X = _cuda(X, torch.float32, "X")
+        Y = torch.empty((X.shape[0], l), device=X.device, dtype=torch.float32)
+        self._check(self.lib.krr_sparse_sketch(self.h, _ptr(X), X.shape[0], X.shape[1], sigma, l, r,
+                                               seed, _ptr(Y)))
+        self._X = None
+        return Y
+
     def qrcp(self, Y, k: int):
         """First k pivots of the column-pivoted QR of Y^T and |R_jj| (Y is consumed)."""
         Y = _cuda(Y, torch.float32, "Y").clone()

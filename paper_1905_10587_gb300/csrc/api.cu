@@ -319,6 +319,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.check_every < 1 || !(ctx->opts.inner_tol > 0.0) || ctx->opts.inner_tol >= 1.0 ||
         ctx->opts.residual < 0 || ctx->opts.residual > 1 || ctx->opts.precision < 0 ||
         ctx->opts.precision > 2 || ctx->opts.escalate < 0 || ctx->opts.escalate > 1 ||
+        ctx->opts.sparse_r < 0 || ctx->opts.sparse_r > 1024 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -525,6 +526,29 @@ int krr_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, i
     return KRR_OK;
 }
 
+int krr_sparse_draw(krr_ctx* ctx, unsigned long long seed, int l, int r, long long n, int* R, float* S) {
+    if (!ctx) return KRR_E_INVAL;
+    if (!R || !S || l < 1 || r < 1 || n < 1 || n > 0x7fffffffLL)
+        return fail(ctx, KRR_E_INVAL, "bad sparse draw arguments");
+    return launch_sparse_draw(ctx, seed, l, r, n, R, S);
+}
+
+int krr_sparse_sketch(krr_ctx* ctx, const float* X, long long n, int d, double sigma, int l, int r,
+                      unsigned long long seed, float* Y) {
+    if (!ctx) return KRR_E_INVAL;
+    KRR_RET(check_points(ctx, X, n, d));
+    KRR_RET(check_sigma_beta(ctx, sigma, 0.0, false));
+    if (!Y || l < 1 || r < 1) return fail(ctx, KRR_E_INVAL, "bad sparse sketch arguments");
+    KRR_RET(build_common(ctx, X, n, d, sigma, 1.0));   // packed points; the build state is reset
+    int* R;
+    float* S;
+    KRR_RET(bufT(ctx, "sp_R", (size_t)l * r, &R));
+    KRR_RET(bufT(ctx, "sp_S", (size_t)l * r, &S));
+    KRR_RET(launch_sparse_draw(ctx, seed, l, r, n, R, S));
+    Phase ph(ctx, PH_SKETCH);
+    return launch_sparse_sketch(ctx, ctx->P, n, d, R, S, l, r, Y, l);
+}
+
 int krr_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int k, int* piv, float* rdiag) {
     if (!ctx) return KRR_E_INVAL;
     if (!Y || !piv || !rdiag || n < 1 || l < 1 || k < 1 || k > n)
@@ -546,7 +570,24 @@ int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double s
     ctx->l = l;
     float* Y;
     int ld;
-    KRR_RET(sketch_internal(ctx, n, l, seed, &Y, &ld, true));
+    if (ctx->opts.sparse_r > 0) {
+        // Algorithm 2: l projections with sparse_r nonzeros each
+        const int r = ctx->opts.sparse_r;
+        int* R;
+        float* S;
+        ld = (l + 3) / 4 * 4;
+        KRR_RET(bufT(ctx, "sketch", (size_t)n * ld, &Y));
+        KRR_RET(bufT(ctx, "sp_R", (size_t)l * r, &R));
+        KRR_RET(bufT(ctx, "sp_S", (size_t)l * r, &S));
+        {
+            Phase ph(ctx, PH_OMEGA);
+            KRR_RET(launch_sparse_draw(ctx, seed, l, r, n, R, S));
+        }
+        Phase ph(ctx, PH_SKETCH);
+        KRR_RET(launch_sparse_sketch(ctx, ctx->P, n, d, R, S, l, r, Y, ld));
+    } else {
+        KRR_RET(sketch_internal(ctx, n, l, seed, &Y, &ld, true));
+    }
     int* piv;
     float* rdiag;
     KRR_RET(bufT(ctx, "piv", (size_t)k, &piv));
@@ -559,7 +600,7 @@ int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double s
     KRR_TRY_CUDA(cudaMemcpyAsync(rd.data(), rdiag, sizeof(float) * k, cudaMemcpyDeviceToHost,
                                  ctx->stream));
     int tc_err = 0;
-    if (ctx->FA) {
+    if (ctx->FA && ctx->opts.sparse_r == 0) {   // the tensor-core sketch ran
         int* err;
         KRR_RET(bufT(ctx, "tc_err", 1, &err));
         KRR_TRY_CUDA(cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -209,6 +209,10 @@ int launch_rect_ff(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc,
 
 // sketch.cu
 int launch_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, int ld, float* OmT);
+// Algorithm 2: index/sign draws (l x r each) and Y = sum over drawn columns (n x ldy)
+int launch_sparse_draw(krr_ctx* ctx, unsigned long long seed, int l, int r, long long n, int* R, float* S);
+int launch_sparse_sketch(krr_ctx* ctx, const float* P, long long n, int d, const int* R, const float* S,
+                         int l, int r, float* Y, int ldy);
 // Out[i*ldo + a] = sum_j K(Pr_i, Pc_j) V[j*ldv + a], a < ncol (FP32 SIMT contraction)
 int launch_kgemm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
                  const float* V, int ldv, int ncol, float* Out, int ldo);

@@ -133,6 +133,90 @@ int launch_omega(krr_ctx* ctx, unsigned long long seed, int l, long long n, int 
     return KRR_OK;
 }
 
+// ------------------------------------------------------------------ Algorithm 2 sketch
+// The draws of Algorithm 2, steps 3-4: for projection i and entry m, Philox4x32-10 with
+// counter (i, m, 0x53505253, 0) and key (seed lo, seed hi); the row index is the high
+// word of r0 * n and the sign is - when the top bit of r1 is set.  Indices are drawn
+// independently (a repeat counts twice).  R, S: l x r.
+__global__ void k_sparse_draw(unsigned long long seed, int l, int r, long long n, int* __restrict__ R,
+                              float* __restrict__ S) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)l * r) return;
+    const unsigned i = (unsigned)(e / r), m = (unsigned)(e - (long long)i * r);
+    const uint4 w = philox4x32_10(make_uint4(i, m, 0x53505253u, 0u),
+                                  make_uint2((unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)));
+    R[e] = (int)(((unsigned long long)w.x * (unsigned long long)n) >> 32);
+    S[e] = (w.y >> 31) ? -1.f : 1.f;
+}
+
+int launch_sparse_draw(krr_ctx* ctx, unsigned long long seed, int l, int r, long long n, int* R, float* S) {
+    const long long tot = (long long)l * r;
+    k_sparse_draw<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(seed, l, r, n, R, S);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+// Algorithm 2, steps 5-6: Y[j * ldy + i] = sum_m K(x_j, x_{R[i, m]}) S[i, m] from the packed
+// points P (expansion form, as the Gaussian sketch).  A CTA takes 128 rows and `lc`
+// projections: the lc x r gathered points sit in shared memory, each thread sums its
+// row's lc outputs, and the 128 x lc block leaves through shared memory row by row.
+constexpr int SP_THREADS = 128;
+__global__ void __launch_bounds__(SP_THREADS)
+k_sparse_sketch(const float* __restrict__ P, long long n, int dk, int ps, const int* __restrict__ R,
+                const float* __restrict__ S, int l, int r, int lc, float* __restrict__ Y, int ldy) {
+    extern __shared__ float ssp[];
+    float* sG = ssp;                           // lc * r * ps gathered points
+    float* sS = sG + (size_t)lc * r * ps;      // lc * r signs
+    float* sO = sS + (size_t)lc * r;           // SP_THREADS x (lc + 1) outputs
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.y * lc;
+    const int nl = min(lc, l - i0);
+    for (int e = tid; e < nl * r; e += SP_THREADS) {
+        const long long src = R[(size_t)i0 * r + e];
+        for (int c = 0; c < ps; ++c) sG[(size_t)e * ps + c] = P[src * ps + c];
+        sS[e] = S[(size_t)i0 * r + e];
+    }
+    __syncthreads();
+    const long long j = (long long)blockIdx.x * SP_THREADS + tid;
+    if (j < n) {
+        const float* xj = P + j * ps;
+        const float aj = xj[dk];
+        for (int ii = 0; ii < nl; ++ii) {
+            float acc = 0.f;
+            for (int m = 0; m < r; ++m) {
+                const float* g = sG + (size_t)(ii * r + m) * ps;
+                float t = aj + g[dk];
+                for (int c = 0; c < dk; ++c) t = fmaf(2.f * xj[c], g[c], t);
+                acc = fmaf(ex2f(t), sS[ii * r + m], acc);
+            }
+            sO[tid * (lc + 1) + ii] = acc;
+        }
+    }
+    __syncthreads();
+    // row by row: lanes write consecutive projections of one row
+    const int lane = tid & 31, w = tid >> 5;
+    for (int rr = w; rr < SP_THREADS; rr += SP_THREADS / 32) {
+        const long long row = (long long)blockIdx.x * SP_THREADS + rr;
+        if (row >= n) continue;
+        for (int ii = lane; ii < nl; ii += 32) Y[row * ldy + i0 + ii] = sO[rr * (lc + 1) + ii];
+    }
+}
+
+int launch_sparse_sketch(krr_ctx* ctx, const float* P, long long n, int d, const int* R, const float* S,
+                         int l, int r, float* Y, int ldy) {
+    const int dk = kernel_dim(d), ps = packed_stride(d);
+    // projections per CTA: as many as 40 KB of shared memory hold (at most 32)
+    const size_t per = (size_t)r * ps * 4 + (size_t)r * 4 + (size_t)SP_THREADS * 4;
+    int lc = (int)std::max<size_t>(1, std::min<size_t>(32, (40u << 10) / per));
+    lc = std::min(lc, l);
+    const size_t smem = (size_t)lc * per + (size_t)SP_THREADS * 4;
+    if (smem > (48u << 10)) return fail(ctx, KRR_E_INVAL, "sparse sketch: r too large for this d");
+    dim3 grid((unsigned)ceil_div(n, SP_THREADS), (unsigned)ceil_div(l, lc));
+    k_sparse_sketch<<<grid, SP_THREADS, smem, ctx->stream>>>(P, n, dk, ps, R, S, l, r, lc, Y, ldy);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
 // ------------------------------------------------------------------ generated-operand GEMM
 constexpr int KG_THREADS = 256;
 constexpr int KG_BM = 128, KG_BN = 128, KG_BK = 16;
