@@ -432,6 +432,23 @@ def cond_bound_id(lam_k1: float, k: int, n: int, beta: float) -> float:
     return 1.0 + 2.0 * lam_k1 * math.sqrt(4.0 * k * (n - k) + 1.0) / beta
 
 
+def condition_table(X: np.ndarray, sigma: float, beta: float, ks, seed: int = 0, l_extra: int = 5):
+    """Section 5.1's experiment on a given point set: cond(K + beta I) and, for each k,
+    the condition of the system preconditioned with Algorithm 1's anchors, next to the
+    Corollary (ID) bound.  Returns a list of dicts (k = 0 is the unpreconditioned row)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    K = kernel_matrix(X, X, sigma)
+    lam = np.linalg.eigvalsh(K)[::-1]
+    rows = [{"k": 0, "cond": (lam[0] + beta) / (max(lam[-1], 0.0) + beta), "bound": None}]
+    for k in ks:
+        S = anchor_selection(X, sigma, k, k + l_extra, seed)
+        mu = preconditioned_spectrum(K, Nystrom(X, S, sigma, beta).ktilde(), beta)
+        rows.append({"k": int(k), "cond": float(mu.max() / mu.min()),
+                     "bound": cond_bound_id(float(lam[k]), int(k), n, beta)})
+    return rows
+
+
 def numerical_rank_bound(q, h: float, delta: float) -> int:
     """Theorem gaussiankernelbound: rho_delta <= prod_i (floor(gamma q_i) + 1), gamma = (2/pi) sqrt(h^-2 ln(1/delta))."""
     gamma = (2.0 / math.pi) * math.sqrt(math.log(1.0 / delta) / (h * h))

@@ -380,3 +380,15 @@ def test_sparse_anchors_are_comparable_to_gaussian_ones():
     e_random = err(np.random.Generator(np.random.PCG64(0)).choice(600, k, replace=False))
     assert e_sparse <= 2 * e_gauss          # 1.69 vs 1.85 here
     assert e_sparse <= 0.5 * e_random       # uniformly random anchors: 7.1
+
+
+def test_condition_table_falls_with_k_and_meets_the_corollary():
+    # Section 5.1's experiment on a small synthetic set: preconditioning lowers the
+    # condition number, more anchors lower it further, and each value sits under the
+    # Corollary (ID) bound
+    X = _pts(400, 2, 9, scale=2.0)
+    rows = O.condition_table(X, 0.4, 1e-2, (10, 30, 60), seed=1)
+    conds = [r["cond"] for r in rows]
+    assert conds[0] > conds[1] > conds[2] > conds[3] >= 1.0
+    for r in rows[1:]:
+        assert r["cond"] <= r["bound"]
