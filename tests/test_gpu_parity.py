@@ -266,6 +266,23 @@ def test_anchor_quality_close_to_oracle(K):
     assert err_gpu <= 2.0 * err_or
 
 
+@pytest.mark.parametrize("sparse_r", [0, 8])
+def test_gpu_anchors_meet_the_corollary_condition_bound(K, sparse_r):
+    # the anchors the GPU picks (Algorithm 1 or 2) precondition K + beta I below the
+    # Corollary (ID) bound 1 + 2 lambda_{k+1} sqrt(4k(n-k)+1) / beta, and far below
+    # the unpreconditioned condition number
+    p = synth.small(n=800, k=40)
+    ctx = K(sparse_r=sparse_r)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=4)
+    S = ctx.anchors().cpu().numpy()
+    Kf = O.kernel_matrix(p.X, p.X, p.sigma)
+    lam = np.linalg.eigvalsh(Kf)[::-1]
+    mu = O.preconditioned_spectrum(Kf, O.Nystrom(p.X, S, p.sigma, p.beta).ktilde(), p.beta)
+    cond = mu.max() / mu.min()
+    assert cond <= O.cond_bound_id(lam[len(S)], len(S), p.n, p.beta)
+    assert cond < 0.1 * (lam[0] + p.beta) / (lam[-1] + p.beta)
+
+
 # ------------------------------------------------------------------ Algorithm 5
 def test_solve_small_config_vs_dense(K):
     p = synth.small()
