@@ -785,7 +785,6 @@ size_t tc_feature_bytes(long long n, int d) {
 typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
                       int, int, int, double*, int*);
 
-int choose_splits_public(int nblk, int ntiles, int slots);
 
 // Q = K(rows, cols) V + beta V using features FA (rows) and FB (cols).
 int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
