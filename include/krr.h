@@ -10,7 +10,8 @@
  *   - the kernel product is the discrete Gauss transform (Section 2.3,
  *     Eq. dscrt_gt), here evaluated exactly in tiles without storing K;
  *     the paper's width h equals sqrt(2) * sigma;
- *   - anchors come from Algorithm 1 (Gaussian sketch + pivoted QR);
+ *   - anchors come from Algorithm 1 (Gaussian sketch + pivoted QR) or, with
+ *     opts.sparse_r > 0, from Algorithm 2 (sparse sketch + pivoted QR);
  *   - the preconditioner is Algorithm 3 (Nystrom factor + Cholesky of
  *     Eq. chol_factor), applied by Algorithm 4 (Woodbury, Eq. woodbury);
  *   - the driver is Algorithm 5 (PCG).
@@ -41,7 +42,7 @@ extern "C" {
 #define KRR_OK        0
 #define KRR_E_INVAL   1   /* bad argument (host-side check; nothing launched)        */
 #define KRR_E_CUDA    2   /* a CUDA runtime call failed                              */
-#define KRR_E_NOTSPD  3   /* an FP64 Cholesky met a pivot <= 0 even after a shift   */
+#define KRR_E_NOTSPD  3   /* an FP64 Cholesky met a pivot <= 0                       */
 #define KRR_E_NOCONV  4   /* tolerance not reached within the iteration limits      */
 #define KRR_E_STATE   5   /* call out of order (e.g. solve before build)             */
 #define KRR_E_NOMEM   6   /* workspace allocation failed                             */
@@ -212,8 +213,9 @@ int krr_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int k, int* piv, float*
 /* ---------------------------------------------------------------------------
  * Algorithms 3-5.
  * ------------------------------------------------------------------------- */
-/* Build the preconditioner (Algorithm 5 steps 1-2: Algorithm 1 then Algorithm 3)
- * for (X, sigma, beta) with k anchors and l = k + opts.oversample projections.
+/* Build the preconditioner (Algorithm 5 steps 1-2: Algorithm 1, or Algorithm 2 when
+ * opts.sparse_r > 0, then Algorithm 3) for (X, sigma, beta) with k anchors and
+ * l = k + opts.oversample projections.
  * X must stay valid and unchanged until the last krr_solve/krr_predict on it. */
 int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double sigma,
                       double beta, int k, unsigned long long seed);
