@@ -1,5 +1,6 @@
-"""Multi-rank logic of bench.py on CPU (gloo, world size 2): replicas draw distinct
-problems, the job time is the slowest rank's, and the reference arm runs on rank 0 only."""
+"""Host logic of bench.py on CPU: with two gloo ranks, replicas draw distinct problems,
+the job time is the slowest rank's and the reference arm runs on rank 0 only; and the
+roofline object's fields and arithmetic."""
 import json
 import os
 import socket
@@ -65,3 +66,27 @@ def test_reference_arm_is_rank0_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--gpus", "2"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_roofline_fields_and_arithmetic():
+    # the roofline object of the bench line: achieved = n^2 pairs / average launch time,
+    # peak = min(FMA-pipe rate / FMA ops per pair, MUFU rate) from unit counts and the clock
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class P:  # the mixture workload's shape without drawing its points
+        n, d, nrhs = 100000, 8, 1
+
+    clocks = {"sm_max_mhz": 2070.0}
+    r = bench.roofline(P, kms=1620.0, kcnt=1000, clocks=clocks, precision=1, sms=152)
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in r
+    assert r["bound"] == "alu" and r["unit"] == "Gpair/s"
+    mufu = 152 * 32 * 2070e6 / 1e9
+    assert r["peak"] == pytest.approx(mufu)
+    assert r["achieved"] == pytest.approx(1e10 / 1.62e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == bench.MEASURED_TRAFFIC[(1, 100000, 8)]
+    r0 = bench.roofline(P, kms=3780.0, kcnt=1000, clocks=clocks, precision=0, sms=152)
+    assert r0["peak"] == pytest.approx(152 * 128 * 2070e6 / 10 / 1e9)   # d + 1 + nrhs FMA ops
+    assert r0["traffic"] is None                                        # not captured for this form
