@@ -1,4 +1,5 @@
-// Batched solves: many independent problems of uneven size.
+// Batched solves: many independent problems of uneven size, each built and solved as one
+// krr_build_precond + krr_solve would be.
 //
 // A small problem (n of a few thousand) cannot fill 152 SMs: its kernel products are a
 // few microseconds and its PCG iterations are bound by launch latency and the per-
