@@ -190,6 +190,36 @@ def qrcp(Yt: np.ndarray, k: int):
     return np.asarray(P[:kk], dtype=np.int64), np.abs(np.diag(R)[:kk])
 
 
+def strong_rrqr(A: np.ndarray, k: int, f: float = 2.0, max_swaps: int = 10_000):
+    """Strong rank-revealing QR (Gu and Eisenstat, 1996), the factorization Section 2.1's
+    interpolative-decomposition bound (Eq. boundid) assumes: start from the pivoted QR
+    and, while some entry of R11^{-1} R12 or some ratio gamma_j(R22) / omega_i(R11)
+    exceeds f in the combined measure
+        (R11^{-1} R12)_ij^2 + (gamma_j / omega_i)^2 > f^2,
+    swap column i of the leading block with column j of the trailing one (gamma_j: norm of
+    column j of R22, omega_i: 1 / norm of row i of R11^{-1}).  Each swap multiplies
+    |det R11| by more than f, so the loop ends.  Returns (perm, swaps): the first k
+    entries of perm are the chosen columns.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[1]
+    _, P = sla.qr(A, mode="r", pivoting=True)
+    perm = np.asarray(P, dtype=np.int64).copy()
+    for swaps in range(max_swaps + 1):
+        R = np.linalg.qr(A[:, perm], mode="r")
+        R11, R12 = R[:k, :k], R[:k, k:]
+        R22 = R[k:, k:]
+        W = sla.solve_triangular(R11, R12)
+        R11inv = sla.solve_triangular(R11, np.eye(k))
+        omega = 1.0 / np.linalg.norm(R11inv, axis=1)
+        gamma = np.linalg.norm(R22, axis=0) if R22.size else np.zeros(n - k)
+        rho = W ** 2 + (gamma[None, :] / omega[:, None]) ** 2
+        i, j = np.unravel_index(int(np.argmax(rho)), rho.shape)
+        if rho[i, j] <= f * f or swaps == max_swaps:
+            return perm, swaps
+        perm[i], perm[k + j] = perm[k + j], perm[i]
+
+
 def qrcp_greedy(Yt: np.ndarray, k: int):
     """The same pivot rule spelled out: repeatedly take the column with the largest
     residual norm and project it out of all columns (modified Gram-Schmidt).

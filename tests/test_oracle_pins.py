@@ -392,3 +392,55 @@ def test_condition_table_falls_with_k_and_meets_the_corollary():
     assert conds[0] > conds[1] > conds[2] > conds[3] >= 1.0
     for r in rows[1:]:
         assert r["cond"] <= r["bound"]
+
+
+# ------------------------------------------------------------- strong RRQR
+def _kahan(n, c):
+    s = math.sqrt(1 - c * c)
+    return np.diag(s ** np.arange(n)) @ (np.eye(n) + np.triu(-c * np.ones((n, n)), 1))
+
+
+def test_strong_rrqr_reveals_the_kahan_matrix_rank_where_pivoted_qr_does_not():
+    # Kahan's matrix (columns scaled by 1 - 1e-10 j so that pivoting keeps their order):
+    # pivoted QR leaves r_nn near 2e-2 while sigma_n is 1e-11; strong RRQR with f = 2
+    # must bring the trailing block under sigma_n sqrt(1 + f^2 k (n - k)) (Gu-Eisenstat)
+    n, k, f = 90, 89, 2.0
+    A = _kahan(n, 0.285) @ np.diag(1 - 1e-10 * np.arange(n))
+    sig = np.linalg.svd(A, compute_uv=False)
+    R0, P0 = sla.qr(A, mode="r", pivoting=True)
+    bound = sig[-1] * math.sqrt(1 + f * f * k * (n - k))
+    assert abs(R0[-1, -1]) > 1e6 * bound
+    perm, swaps = O.strong_rrqr(A, k, f)
+    assert swaps >= 1
+    R = np.linalg.qr(A[:, perm], mode="r")
+    assert abs(R[-1, -1]) <= bound * (1 + 1e-6)
+
+
+def test_strong_rrqr_meets_its_bounds_on_a_sketch():
+    # on a Gaussian sketch of a kernel matrix: |R11^{-1} R12| <= f and the singular values
+    # of R11 and R22 within sqrt(1 + f^2 k (n - k)) of those of A
+    X = _pts(120, 2, 12, scale=2.0)
+    A = O.sketch(X, 0.5, O.omega(3, 25, 120)).T          # l x n, columns = points
+    k, f = 20, 2.0
+    perm, _ = O.strong_rrqr(A, k, f)
+    R = np.linalg.qr(A[:, perm], mode="r")
+    W = sla.solve_triangular(R[:k, :k], R[:k, k:])
+    assert np.abs(W).max() <= f * (1 + 1e-9)
+    n = A.shape[1]
+    fac = math.sqrt(1 + f * f * k * (n - k))
+    sA = np.linalg.svd(A, compute_uv=False)
+    s11 = np.linalg.svd(R[:k, :k], compute_uv=False)
+    s22 = np.linalg.svd(R[k:, k:], compute_uv=False)
+    assert np.all(s11 >= sA[:k] / fac * (1 - 1e-9))
+    assert np.all(s22[:len(sA) - k] <= sA[k:k + len(s22)] * fac * (1 + 1e-9) + 1e-14)
+
+
+def test_pivoted_qr_of_kernel_sketches_already_meets_strong_rrqr():
+    # Section 3's remark (pivoted QR works in practice): on Gaussian kernel sketches the
+    # pivoted QR's first k columns already satisfy the strong RRQR conditions with f = 2,
+    # so no swap is needed and the ID bound of Eq. boundid holds for the GPU's pivot rule
+    for seed, (n, d, sigma, l, k) in enumerate([(120, 2, 0.5, 25, 20), (600, 4, 0.5, 105, 100)]):
+        X = np.random.Generator(np.random.PCG64(seed)).uniform(0, 2, size=(n, d))
+        A = O.sketch(X, sigma, O.omega(3, l, n)).T
+        _, swaps = O.strong_rrqr(A, k, 2.0)
+        assert swaps == 0
