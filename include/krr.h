@@ -6,14 +6,14 @@
  * by preconditioned conjugate gradient, following Shabat, Choshen, Ben-Or and
  * Carmel, "Fast and Accurate Gaussian Kernel Ridge Regression Using Matrix
  * Decompositions for Preconditioning" (arXiv 1905.10587):
- *   - the problem is Eq. (1) and Eq. (ridge_regression) of Section 1;
- *   - the kernel product is the discrete Gauss transform (Section 2.3,
- *     Eq. dscrt_gt), here evaluated exactly in tiles without storing K;
+ *   - the problem is Eq. (1) and Eq. (2) of Section 1;
+ *   - the kernel product is the discrete Gauss transform (Section 2.4,
+ *     Eq. (6)), here evaluated exactly in tiles without storing K;
  *     the paper's width h equals sqrt(2) * sigma;
  *   - anchors come from Algorithm 1 (Gaussian sketch + pivoted QR) or, with
  *     opts.sparse_r > 0, from Algorithm 2 (sparse sketch + pivoted QR);
  *   - the preconditioner is Algorithm 3 (Nystrom factor + Cholesky of
- *     Eq. chol_factor), applied by Algorithm 4 (Woodbury, Eq. woodbury);
+ *     Eq. (10)), applied by Algorithm 4 (Woodbury, Eq. (7));
  *   - the driver is Algorithm 5 (PCG).
  *
  * Conventions (all entry points):
@@ -46,7 +46,10 @@ extern "C" {
 #define KRR_E_NOCONV  4   /* tolerance not reached within the iteration limits      */
 #define KRR_E_STATE   5   /* call out of order (e.g. solve before build)             */
 #define KRR_E_NOMEM   6   /* workspace allocation failed                             */
-#define KRR_E_NONFINITE 7 /* NaN or Inf met in an input or a reduction               */
+#define KRR_E_NONFINITE 7 /* NaN or Inf met in an input or a reduction, or PCG met
+                             non-positive curvature it could not recover from         */
+#define KRR_E_TIMEOUT 8   /* a bounded device wait ran out (the kernel stopped, freed
+                             its resources and returned; the context stays usable)   */
 
 #define KRR_MAX_DIM  64
 #define KRR_MAX_RHS  16
@@ -78,7 +81,14 @@ typedef struct krr_opts {
                              product to precision 2 and restart from the current alpha  */
     int    sparse_r;      /* 0 (default): Gaussian sketch (Algorithm 1); r > 0: sparse
                              sketch of Algorithm 2 with r nonzeros per projection (<= 1024) */
-    int    reserved[2];
+    int    wait_limit_log2;   /* bounded device waits of the tensor-core product give up
+                                 after 2^wait_limit_log2 cycles and report KRR_E_TIMEOUT;
+                                 0 (default) = 2^32 cycles (about 2 s); 10..40 allowed.
+                                 Small values are for failure-detection tests            */
+    int    test_stall_copies; /* failure-detection tests only: 1 makes the tensor-core
+                                 product issue no copies, so its bounded waits run out
+                                 (nothing is in flight) and the call returns
+                                 KRR_E_TIMEOUT; 0 (default) in all other use             */
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -143,7 +153,7 @@ int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream);
 int krr_peak_probe(int kind, double* ops_per_s, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Kernel products (Section 2.3, Eq. dscrt_gt; Definition figtree_def).
+ * Kernel products (Section 2.4, Eq. (6); Definition 2.1).
  * Q = K(Xr, Xc) V + beta * V[0:nr]   (Q: nr x nrhs, V: nc x nrhs, RHS-major).
  * K(Xr, Xc)_ij = exp(-||xr_i - xc_j||^2 / (2 sigma^2)), evaluated in FP32 tiles
  * from the expansion ||x||^2 + ||y||^2 - 2 x.y after centring both sets on the
@@ -227,7 +237,7 @@ int krr_build_precond_anchors(krr_ctx* ctx, const float* X, long long n, int d, 
 /* Anchors kept by the last build: writes k_eff (host) and S (device int32[k_eff], may be NULL). */
 int krr_get_anchors(krr_ctx* ctx, int* S, int* k_eff);
 
-/* Out = (K~ + beta I)^{-1} In (Algorithm 4; Eq. woodbury), In/Out n x nrhs FP32. */
+/* Out = (K~ + beta I)^{-1} In (Algorithm 4; Eq. (7)), In/Out n x nrhs FP32. */
 int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out);
 
 /* Solve (K + beta I) alpha = Y (Algorithm 5 step 3) for the built X to
@@ -236,9 +246,13 @@ int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out);
  * FP32 with reliable updates: its recursive residual is replaced by the true one
  * (and its iterate folded into the FP64 alpha) each time it drops by
  * opts.inner_tol.  X must be the pointer given to the build.  alpha: n x nrhs FP64.
- * info (host) may be NULL.  Returns KRR_E_NOCONV if the limits are hit first;
- * alpha then holds, per column, the iterate with the smallest true residual seen
- * (info->rel_residual reports that residual). */
+ * info (host) may be NULL.  Returns KRR_E_NOCONV if the limits are hit first, or
+ * KRR_E_NONFINITE if PCG breaks down (non-positive curvature or a non-finite value)
+ * in a form it cannot escalate from; in both cases alpha holds, per column, the
+ * iterate with the smallest verified true residual seen (info->rel_residual reports
+ * that residual).  When PCG meets non-positive curvature in product form 0 or 1 with
+ * opts.escalate set, the unverified correction since the last true residual is
+ * discarded and the solve goes on in form 2 from the best verified alpha. */
 int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol,
               double* alpha, krr_solve_info* info);
 
@@ -247,10 +261,14 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
  * exists for callers that may not allocate device memory, such as an
  * application that owns all GPU memory through its own pool, or code running
  * where a cudaMalloc is not allowed.  It computes the same product as krr_kmvm
- * (no context needed), taking all temporaries from one fixed device
- * array of KRR_NOALLOC_SCRATCH_BYTES that every GPU loading this library keeps
- * until the process exits.  The first call on a device looks up that array's
- * device address, so make that first call before any stream capture.  Calls
+ * (no context needed), taking all temporaries from one fixed device array of
+ * KRR_NOALLOC_SCRATCH_BYTES that every GPU which runs this call keeps until the
+ * process exits.  The array's device address belongs to the CUDA context it was
+ * looked up in: the first call on a device (and the first after that device's
+ * context is replaced, e.g. by cudaDeviceReset) looks it up with that context
+ * current, and under lazy module loading that lookup is what commits the array's
+ * memory.  So make the first call before memory runs short and before any stream
+ * capture; if the array cannot be committed then, KRR_E_NOMEM is returned.  Calls
  * share the array: calls whose work overlaps on the GPU (other streams, other
  * threads) race on it and must be serialised by the caller.  No temporary needs
  * to start at zero.  If a size needs more scratch than the array holds, nothing

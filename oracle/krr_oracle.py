@@ -14,7 +14,7 @@ scipy.linalg.qr with column pivoting (LAPACK dgeqp3).
 
 Kernel convention: K_ij = exp(-||x_i - x_j||^2 / (2 sigma^2)).  The paper's
 Gaussian is exp(-||x - y||^2 / h^2) (Eq. of the discrete Gauss transform,
-Section 2.3), so h = sqrt(2) sigma.  Parameters named ``h`` below are the
+Section 2.4), so h = sqrt(2) sigma.  Parameters named ``h`` below are the
 paper's width; everything else takes sigma.
 
 Readings where the paper is silent or garbled (all listed in the design notes):
@@ -24,10 +24,10 @@ Readings where the paper is silent or garbled (all listed in the design notes):
   * U^(1/2) is built from an EVD of K_SS = U^(-1), truncated at
     tau = k * eps64 * lambda_max, so that U = K_SS^+ (Section 2.2 defines the
     Nystrom U through a pseudo-inverse).
-  * The Cholesky factor of Eq. (chol_factor) is taken upper triangular so that
+  * The Cholesky factor of Eq. (10) is taken upper triangular so that
     L^T L equals the printed product.
   * Algorithm 3, step 4 is read as Y = C U^(1/2) (n x k), the only order
-    consistent with Eq. (chol_factor).
+    consistent with Eq. (10).
   * CG is the textbook preconditioned CG; the true residual replaces the
     recursive one every 50 iterations.
   * The random test matrix is drawn with Philox4x32-10 (Salmon et al., SC'11)
@@ -47,7 +47,7 @@ EPS64 = np.finfo(np.float64).eps
 
 
 # ----------------------------------------------------------------------------
-# Kernel matrix and its products (Section 1, Eq. (1) and Remark 1; Section 2.3)
+# Kernel matrix and its products (Section 1, Eq. (1) and Remark 1.1; Section 2.4)
 # ----------------------------------------------------------------------------
 def sqdist(A: np.ndarray, B: np.ndarray) -> np.ndarray:
     """Pairwise squared distances ||a_i - b_j||^2 from explicit differences."""
@@ -61,13 +61,13 @@ def sqdist(A: np.ndarray, B: np.ndarray) -> np.ndarray:
 
 
 def kernel_matrix(A: np.ndarray, B: np.ndarray, sigma: float) -> np.ndarray:
-    """K_ij = exp(-||a_i - b_j||^2 / (2 sigma^2)) (Remark 1; Eq. dscrt_gt with h^2 = 2 sigma^2)."""
+    """K_ij = exp(-||a_i - b_j||^2 / (2 sigma^2)) (Remark 1.1; Eq. (6) with h^2 = 2 sigma^2)."""
     return np.exp(-sqdist(A, B) / (2.0 * sigma * sigma))
 
 
 def kmvm(X: np.ndarray, V: np.ndarray, sigma: float, beta: float = 0.0,
          rows: np.ndarray | None = None, block: int = 16) -> np.ndarray:
-    """(K + beta I) V, restricted to ``rows`` if given (the discrete Gauss transform, Eq. dscrt_gt).
+    """(K + beta I) V, restricted to ``rows`` if given (the discrete Gauss transform, Eq. (6)).
 
     Rows are evaluated a few at a time straight from the definition, so this
     works at any n without forming K.  V is (n, nrhs) or (n,).
@@ -86,7 +86,7 @@ def kmvm(X: np.ndarray, V: np.ndarray, sigma: float, beta: float = 0.0,
 
 def kmvm_rect(Xr: np.ndarray, Xc: np.ndarray, V: np.ndarray, sigma: float,
               block: int = 64) -> np.ndarray:
-    """K(Xr, Xc) V for two point sets (Definition figtree_def: FIG(Xc, Xr, h, V))."""
+    """K(Xr, Xc) V for two point sets (Definition 2.1: FIG(Xc, Xr, h, V))."""
     V = np.asarray(V, dtype=np.float64)
     vec = V.ndim == 1
     V2 = V[:, None] if vec else V
@@ -102,7 +102,7 @@ def predict(Xtest: np.ndarray, X: np.ndarray, alpha: np.ndarray, sigma: float) -
 
 
 def solve_dense(X: np.ndarray, Y: np.ndarray, sigma: float, beta: float) -> np.ndarray:
-    """alpha = (K + beta I)^{-1} y by dense Cholesky (Eq. ridge_regression)."""
+    """alpha = (K + beta I)^{-1} y by dense Cholesky (Eq. (2))."""
     K = kernel_matrix(X, X, sigma)
     K[np.diag_indices_from(K)] += beta
     c = sla.cho_factor(K, lower=True)
@@ -191,8 +191,8 @@ def qrcp(Yt: np.ndarray, k: int):
 
 
 def strong_rrqr(A: np.ndarray, k: int, f: float = 2.0, max_swaps: int = 10_000):
-    """Strong rank-revealing QR (Gu and Eisenstat, 1996), the factorization Section 2.1's
-    interpolative-decomposition bound (Eq. boundid) assumes: start from the pivoted QR
+    """Strong rank-revealing QR (Gu and Eisenstat, 1996), the factorization Section 2.3's
+    interpolative-decomposition bound (Eq. (4)) assumes: start from the pivoted QR
     and, while some entry of R11^{-1} R12 or some ratio gamma_j(R22) / omega_i(R11)
     exceeds f in the combined measure
         (R11^{-1} R12)_ij^2 + (gamma_j / omega_i)^2 > f^2,
@@ -322,35 +322,45 @@ def sparse_anchor_selection(X: np.ndarray, sigma: float, k: int, l: int, r: int,
 # Algorithm 3 (BuildCholesky) and Algorithm 4 (ApplyPreconditioner)
 # ----------------------------------------------------------------------------
 class Nystrom:
-    """Preconditioner (K~ + beta I)^{-1} with K~ = C U C^T, U = K_SS^+ (Section 3, Eq. woodbury)."""
+    """The preconditioner (K~ + beta I)^{-1} of Section 3 for the Nystrom approximation
+    K~ = C U C^T on the anchor set S (Algorithms 3 and 4; Eqs. (7) and (10)).
+
+    C = K(X, X_S) holds the anchor columns and U = K_SS^+ (Section 2.2 defines U through
+    a pseudo-inverse).  With a symmetric square root U^{1/2} of U and F = C U^{1/2}, K~ is
+    F F^T, and the Woodbury identity (Eq. (7)) turns the n x n inverse into a k x k one:
+        (F F^T + beta I)^{-1} = (I - F G^{-1} F^T) / beta,   G = beta I + F^T F,
+    where G is factored once by Cholesky as L^T L with L upper triangular (Eq. (10)).
+    U^{1/2} comes from the eigendecomposition of K_SS, eigenvalues below
+    k eps64 lambda_max being treated as zero (so U is the pseudo-inverse).
+    """
 
     def __init__(self, X: np.ndarray, S: np.ndarray, sigma: float, beta: float):
         X = np.asarray(X, dtype=np.float64)
         self.X, self.S, self.sigma, self.beta = X, np.asarray(S), sigma, beta
-        XS = X[self.S]                                       # Alg. 3 step 1
-        Uinv = kernel_matrix(XS, XS, sigma)                  # Alg. 3 step 2: U^{-1} = K_SS
-        lam, Vec = np.linalg.eigh(Uinv)                      # Alg. 3 step 3 (EVD)
+        XS = X[self.S]
+        Kss = kernel_matrix(XS, XS, sigma)                   # K_SS = U^{-1}
+        lam, Vec = np.linalg.eigh(Kss)
         keep = lam > len(self.S) * EPS64 * lam.max()
         root = np.zeros_like(lam)
         root[keep] = 1.0 / np.sqrt(lam[keep])
-        self.Uhalf = (Vec * root) @ Vec.T                    # U^{1/2} with U = K_SS^+
-        self.C = kernel_matrix(X, XS, sigma)                 # C = K[:, S]
-        Yb = self.C @ self.Uhalf                             # Alg. 3 step 4: Y = C U^{1/2}
-        G = beta * np.eye(len(self.S)) + self.Uhalf @ (self.C.T @ Yb)   # step 5
-        self.L = sla.cholesky(G, lower=False)                # step 6: G = L^T L (L upper)
+        self.Uhalf = (Vec * root) @ Vec.T                    # U^{1/2}, U = K_SS^+
+        self.C = kernel_matrix(X, XS, sigma)                 # C = K(X, X_S)
+        F = self.C @ self.Uhalf                              # K~ = F F^T
+        G = beta * np.eye(len(self.S)) + self.Uhalf @ (self.C.T @ F)   # beta I + F^T F
+        self.L = sla.cholesky(G, lower=False)                # G = L^T L
 
     def ktilde(self) -> np.ndarray:
         F = self.C @ self.Uhalf
         return F @ F.T
 
     def apply(self, x: np.ndarray) -> np.ndarray:
-        """Algorithm 4: y = U^{1/2} C^T x; L^T L z' = y; z = U^{1/2} z'; r = x/beta - C z / beta."""
+        """(K~ + beta I)^{-1} x = (x - F G^{-1} F^T x) / beta, with F^T x = U^{1/2} (C^T x)
+        and G^{-1} applied through the two triangular solves of G = L^T L."""
         x = np.asarray(x, dtype=np.float64)
-        y = self.Uhalf @ (self.C.T @ x)
-        w = sla.solve_triangular(self.L, y, trans="T", lower=False)
-        zp = sla.solve_triangular(self.L, w, lower=False)
-        z = self.Uhalf @ zp
-        return x / self.beta - (self.C @ z) / self.beta
+        u = self.Uhalf @ (self.C.T @ x)                      # F^T x
+        w = sla.solve_triangular(self.L, u, trans="T", lower=False)
+        v = sla.solve_triangular(self.L, w, lower=False)     # G^{-1} F^T x
+        return x / self.beta - (self.C @ (self.Uhalf @ v)) / self.beta
 
 
 # ----------------------------------------------------------------------------
@@ -452,20 +462,20 @@ def val_mse(X, y, Xv, yv, sigma, beta) -> float:
 # Theory helpers (Section 4)
 # ----------------------------------------------------------------------------
 def preconditioned_spectrum(K: np.ndarray, Ktilde: np.ndarray, beta: float) -> np.ndarray:
-    """Eigenvalues of (K~ + beta I)^{-1}(K + beta I) as a generalized symmetric problem (Theorem maintheorem)."""
+    """Eigenvalues of (K~ + beta I)^{-1}(K + beta I) as a generalized symmetric problem (Theorem 4.5)."""
     n = K.shape[0]
     return sla.eigh(K + beta * np.eye(n), Ktilde + beta * np.eye(n), eigvals_only=True)
 
 
 def cond_bound_id(lam_k1: float, k: int, n: int, beta: float) -> float:
-    """Corollary (ID): cond <= 1 + 2 lambda_{k+1} sqrt(4k(n-k)+1) / beta."""
+    """Corollary 4.10: cond <= 1 + 2 lambda_{k+1} sqrt(4k(n-k)+1) / beta."""
     return 1.0 + 2.0 * lam_k1 * math.sqrt(4.0 * k * (n - k) + 1.0) / beta
 
 
 def condition_table(X: np.ndarray, sigma: float, beta: float, ks, seed: int = 0, l_extra: int = 5):
     """Section 5.1's experiment on a given point set: cond(K + beta I) and, for each k,
     the condition of the system preconditioned with Algorithm 1's anchors, next to the
-    Corollary (ID) bound.  Returns a list of dicts (k = 0 is the unpreconditioned row)."""
+    Corollary 4.10 bound.  Returns a list of dicts (k = 0 is the unpreconditioned row)."""
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
     K = kernel_matrix(X, X, sigma)
@@ -480,29 +490,29 @@ def condition_table(X: np.ndarray, sigma: float, beta: float, ks, seed: int = 0,
 
 
 def numerical_rank_bound(q, h: float, delta: float) -> int:
-    """Theorem gaussiankernelbound: rho_delta <= prod_i (floor(gamma q_i) + 1), gamma = (2/pi) sqrt(h^-2 ln(1/delta))."""
+    """Theorem 4.4: rho_delta <= prod_i (floor(gamma q_i) + 1), gamma = (2/pi) sqrt(h^-2 ln(1/delta))."""
     gamma = (2.0 / math.pi) * math.sqrt(math.log(1.0 / delta) / (h * h))
     return int(np.prod([math.floor(gamma * qi) + 1 for qi in q]))
 
 
 def tradeoff_gamma(h: float, n: float, beta: float, xi: float, Mbar: float) -> float:
-    """The gamma of Corollary tradeoff: (2/pi) sqrt(h^-2 ln(Mbar n / (beta (xi - 1))))."""
+    """The gamma of Corollary 4.6: (2/pi) sqrt(h^-2 ln(Mbar n / (beta (xi - 1))))."""
     return (2.0 / math.pi) * math.sqrt(math.log(Mbar * n / (beta * (xi - 1.0))) / (h * h))
 
 
 def tradeoff_rank(q, h: float, n: float, beta: float, xi: float, Mbar: float) -> int:
-    """Corollary tradeoff, Eq. condbound: k >= prod_i (floor(q_i gamma) + 1)."""
+    """Corollary 4.6, Eq. (24): k >= prod_i (floor(q_i gamma) + 1)."""
     g = tradeoff_gamma(h, n, beta, xi, Mbar)
     return int(np.prod([math.floor(qi * g) + 1 for qi in q], dtype=object))
 
 
 def iters_unpreconditioned(lam1: float, beta: float, delta: float) -> float:
-    """Eq. noprecond_rate: i ~ -sqrt(lambda_1) ln(delta) / (2 sqrt(beta))."""
+    """Eq. (31): i ~ -sqrt(lambda_1) ln(delta) / (2 sqrt(beta))."""
     return -math.sqrt(lam1) * math.log(delta) / (2.0 * math.sqrt(beta))
 
 
 def iters_preconditioned(M: float, lam_k1: float, beta: float, delta: float) -> float:
-    """Eq. precond_rate2: i = ln(delta) / ln((sqrt(beta + M lam) - sqrt(beta)) / (sqrt(beta + M lam) + sqrt(beta)))."""
+    """Eq. (33): i = ln(delta) / ln((sqrt(beta + M lam) - sqrt(beta)) / (sqrt(beta + M lam) + sqrt(beta)))."""
     a = math.sqrt(beta + M * lam_k1)
     b = math.sqrt(beta)
     return math.log(delta) / math.log((a - b) / (a + b))

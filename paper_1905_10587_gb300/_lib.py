@@ -16,17 +16,18 @@ KRR_MAX_DIM = 64
 
 STATUS = {
     0: "KRR_OK", 1: "KRR_E_INVAL", 2: "KRR_E_CUDA", 3: "KRR_E_NOTSPD", 4: "KRR_E_NOCONV",
-    5: "KRR_E_STATE", 6: "KRR_E_NOMEM", 7: "KRR_E_NONFINITE",
+    5: "KRR_E_STATE", 6: "KRR_E_NOMEM", 7: "KRR_E_NONFINITE", 8: "KRR_E_TIMEOUT",
 }
 KRR_OK, KRR_E_INVAL, KRR_E_CUDA, KRR_E_NOTSPD, KRR_E_NOCONV = 0, 1, 2, 3, 4
-KRR_E_STATE, KRR_E_NOMEM, KRR_E_NONFINITE = 5, 6, 7
+KRR_E_STATE, KRR_E_NOMEM, KRR_E_NONFINITE, KRR_E_TIMEOUT = 5, 6, 7, 8
 
 
 class KrrOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("refine_max", C.c_int), ("oversample", C.c_int),
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
-                ("escalate", C.c_int), ("sparse_r", C.c_int), ("reserved", C.c_int * 2)]
+                ("escalate", C.c_int), ("sparse_r", C.c_int), ("wait_limit_log2", C.c_int),
+                ("test_stall_copies", C.c_int)]
 
 
 class KrrSolveInfo(C.Structure):

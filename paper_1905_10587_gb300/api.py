@@ -104,7 +104,7 @@ class KRR:
 
     # ---------------------------------------------------------------- products
     def kmvm(self, Xr, Xc, V, sigma: float, beta: float = 0.0) -> torch.Tensor:
-        """K(Xr, Xc) V + beta V (Section 2.3, Eq. dscrt_gt)."""
+        """K(Xr, Xc) V + beta V (Section 2.4, Eq. (6))."""
         Xr = _cuda(Xr, torch.float32, "Xr")
         Xc = _cuda(Xc, torch.float32, "Xc")
         Vt, vec = _cols(V, torch.float32, "V")

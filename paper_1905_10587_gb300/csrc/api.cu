@@ -320,6 +320,9 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.residual < 0 || ctx->opts.residual > 1 || ctx->opts.precision < 0 ||
         ctx->opts.precision > 2 || ctx->opts.escalate < 0 || ctx->opts.escalate > 1 ||
         ctx->opts.sparse_r < 0 || ctx->opts.sparse_r > 1024 ||
+        (ctx->opts.wait_limit_log2 != 0 &&
+         (ctx->opts.wait_limit_log2 < 10 || ctx->opts.wait_limit_log2 > 40)) ||
+        ctx->opts.test_stall_copies < 0 || ctx->opts.test_stall_copies > 1 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -439,13 +442,14 @@ int krr_kmvm(krr_ctx* ctx, const float* Xr, long long nr, const float* Xc, long 
         KRR_RET(bufT(ctx, "kmvm_FB", tc_feature_bytes(nc, d), &FB));
         KRR_RET(launch_tc_features(ctx, Pr, nr, d, 0, FA));
         KRR_RET(launch_tc_features(ctx, Pc, nc, d, 1, FB));
-        KRR_RET(launch_kmvm_tc(ctx, FA, nr, FB, nc, d, (float)beta, V, nrhs, Q));
         int* err;
         int herr = 0;
         KRR_RET(bufT(ctx, "tc_err", 1, &err));
+        KRR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+        KRR_RET(launch_kmvm_tc(ctx, FA, nr, FB, nc, d, (float)beta, V, nrhs, Q));
         KRR_TRY_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-        if (herr) return fail(ctx, KRR_E_CUDA, "tensor-core product: a bounded wait timed out");
+        if (herr) return fail(ctx, KRR_E_TIMEOUT, "tensor-core product: a bounded wait timed out");
         return KRR_OK;
     }
     KRR_RET(launch_kmvm(ctx, Pr, nr, Pc, nc, d, (float)beta, V, nrhs, Q));
@@ -606,7 +610,7 @@ int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double s
         KRR_TRY_CUDA(cudaMemcpyAsync(&tc_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     }
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (tc_err) return fail(ctx, KRR_E_CUDA, "tensor-core sketch: a bounded wait timed out");
+    if (tc_err) return fail(ctx, KRR_E_TIMEOUT, "tensor-core sketch: a bounded wait timed out");
     int k_eff = 0;
     const float thr = (float)(ctx->opts.anchor_rtol * rd[0]);
     while (k_eff < k && rd[k_eff] > thr && std::isfinite(rd[k_eff])) ++k_eff;
@@ -781,6 +785,13 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         return KRR_OK;
     };
 
+    // error word of the tensor-core product (set when one of its bounded waits ran out);
+    // read with the CG scalars, into the pinned tail of the scalar mirror
+    int* tc_err_dev = nullptr;
+    KRR_RET(bufT(ctx, "tc_err", 1, &tc_err_dev));
+    int* tc_err_host = &ctx->cg_host->tc_err;
+    *tc_err_host = 0;
+    KRR_TRY_CUDA(cudaMemsetAsync(tc_err_dev, 0, sizeof(int), ctx->stream));
     KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
     KRR_RET(true_residual(true));
     if (!any_active()) {
@@ -813,14 +824,29 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             if (it % ctx->opts.check_every == 0 || last) {
                 KRR_TRY_CUDA(cudaMemcpyAsync(ctx->cg_host, ctx->cg, sizeof(CGScalars),
                                              cudaMemcpyDeviceToHost, ctx->stream));
+                if (form == 1)
+                    KRR_TRY_CUDA(cudaMemcpyAsync(tc_err_host, tc_err_dev, sizeof(int),
+                                                 cudaMemcpyDeviceToHost, ctx->stream));
                 KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+                if (form == 1 && *tc_err_host) {
+                    status = KRR_E_TIMEOUT;
+                    fail(ctx, status, "tensor-core product: a bounded wait timed out");
+                    break;
+                }
                 bool escalate = false;
                 if (ctx->cg_host->bad) {
                     if (!ctx->opts.escalate || form == 2 || last) {
-                        fail(ctx, KRR_E_NONFINITE, "non-positive curvature or non-finite value in PCG");
+                        status = KRR_E_NONFINITE;
+                        fail(ctx, status, "non-positive curvature or non-finite value in PCG");
                         break;
                     }
+                    // The correction x was built on an operator that is not positive
+                    // definite in FP32: it is unverified and is discarded, and the solve
+                    // goes on from the best verified alpha of every column.
                     escalate = true;
+                    KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+                    KRR_TRY_CUDA(cudaMemcpyAsync(alpha, abest, sizeof(double) * tot,
+                                                 cudaMemcpyDeviceToDevice, ctx->stream));
                 }
                 bool update = last || escalate || since >= window;
                 for (int c = 0; c < nrhs; ++c) {
@@ -902,7 +928,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     inf.product_form = form;
     inf.solve_ms = now_ms() - t0;
     if (info) *info = inf;
-    if (status != KRR_OK) fail(ctx, status, "tolerance not reached");
+    if (status == KRR_E_NOCONV) fail(ctx, status, "tolerance not reached");
     return status;
 }
 

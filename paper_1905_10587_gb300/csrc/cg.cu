@@ -1,5 +1,5 @@
 // Conjugate-gradient vector kernels (Algorithm 5 step 3) and the Woodbury
-// application of the preconditioner (Algorithm 4, Eq. woodbury).
+// application of the preconditioner (Algorithm 4, Eq. (7)).
 //
 // Vectors are FP32, RHS-major (column q of an n x nrhs block at q*n); every dot
 // product is accumulated in FP64 and the CG scalars live in a small device struct,

@@ -1,4 +1,4 @@
-// FP64 k x k linear algebra of the preconditioner build (Algorithm 3, Eq. chol_factor):
+// FP64 k x k linear algebra of the preconditioner build (Algorithm 3, Eq. (10)):
 // the anchor kernel block K_SS, blocked right-looking Cholesky, triangular
 // inversion by blocked forward substitution, and small helpers.  All matrices are
 // row-major k x k.  k is at most a few thousand, so these run a few hundred

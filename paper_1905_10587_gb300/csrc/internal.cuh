@@ -64,6 +64,7 @@ struct CGScalars {
     int active[KRR_MAX_RHS];
     int all_done;
     int bad;            // a non-finite or non-positive curvature was met
+    int tc_err;         // host mirror only: the tensor-core product's error word
 };
 
 struct Buf {

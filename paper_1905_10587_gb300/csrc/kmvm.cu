@@ -1,5 +1,5 @@
 // Tiled on-the-fly Gaussian kernel products (the discrete Gauss transform of
-// Section 2.3, Eq. dscrt_gt, evaluated exactly): K is never stored.
+// Section 2.4, Eq. (6), evaluated exactly): K is never stored.
 //
 //   Q_i = sum_j exp2(a_i + a_j + 2 xh_i . xh_j) V_j  (+ beta V_i)
 //
@@ -659,8 +659,9 @@ int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float*
 // ------------------------------------------------------------------ product into given scratch
 // The FP32 product K(Xr, Xc) V + beta V with every temporary (mean, packed points,
 // split-K partial sums) carved from one caller-provided device buffer: no device
-// allocation and no context.  Returns KRR_E_INVAL with *needed set when the buffer
-// is too small.
+// allocation and no context.  *needed receives the bytes this size takes; returns
+// KRR_E_NOMEM when the buffer is too small for it, KRR_E_INVAL when no compiled tile
+// serves (d, nrhs), KRR_E_CUDA when a launch fails.
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long long nr,
@@ -677,7 +678,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
         const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         int R = 4;
         kmvm_fn fn = pick(dk, chunk, &R);
-        if (!fn) return KRR_E_INVAL;
+        if (!fn) return KRR_E_INVAL;   // no compiled tile for this (d, chunk): not a size problem
         int occ = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, KM_THREADS, 0) !=
                 cudaSuccess || occ < 1)
@@ -697,7 +698,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
     const size_t off_part = off_pr + (same ? 0 : align256(sizeof(float) * (size_t)nr * ps));
     const size_t total = off_part + align256(sizeof(double) * part_elems);
     if (needed) *needed = total;
-    if (total > cap) return KRR_E_INVAL;
+    if (total > cap) return KRR_E_NOMEM;   // the fixed scratch is too small for this size
 
     double* mpart = reinterpret_cast<double*>(scratch + off_mpart);
     double* mu = reinterpret_cast<double*>(scratch + off_mu);

@@ -6,10 +6,14 @@
 //   * x_i . x_j is summed exactly term by term (FMA two-product + Knuth two-sum),
 //     and ||x_i - x_j||^2 = n_i + n_j - 2 x_i . x_j with float-float norms;
 //   * t = -s ||x_i - x_j||^2 with s = log2(e) / (2 sigma^2) in float-float;
-//   * 2^t = 2^m * 2^(j/64) * e^z: m = round(t), j = round(64 (t - m)) picks an
-//     entry of a 65-entry float-float table of 2^(j/64) (built on the host in
-//     double), and e^z with |z| <= ln2/128 is 1 + z + ... + z^5/120 (truncation
-//     below 4e-17); the low word of t enters as the factor (1 + ln2 t_lo);
+//   * 2^t by the table-driven reduction of P. T. P. Tang, "Table-driven
+//     implementation of the exponential function in IEEE floating-point
+//     arithmetic", ACM TOMS 15(2), 1989, carried in float-float:
+//     2^t = 2^m * 2^(j/64) * e^z with m = round(t), j = round(64 (t - m)) picking
+//     an entry of a 65-entry float-float table of 2^(j/64) (built on the host in
+//     double), and e^z with |z| <= ln2/128 evaluated as its Taylor polynomial
+//     1 + z + ... + z^5/120 (truncation below 4e-17); the low word of t enters as
+//     the factor (1 + ln2 t_lo);
 //   * K_ij A_j is formed exactly (two-product), summed in float-float over a
 //     tile of 64 columns and folded into an FP64 accumulator per tile.
 // Relative error of each kernel value is a few 1e-12, against ~1e-7 for the FP32

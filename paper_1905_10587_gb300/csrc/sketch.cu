@@ -1,6 +1,6 @@
 // Algorithm 1 step 1-2 (the Gaussian test matrix and the sketch Y = K Omega^T),
 // the contraction F = K(X, X_S) W used by Algorithm 3, and the Gram matrix
-// G = beta I + F^T F of Eq. (chol_factor).
+// G = beta I + F^T F of Eq. (10).
 //
 // The two contractions have the shape of a GEMM whose left operand is produced on
 // the fly: each K-step generates a BK x BM tile of kernel values exp2(a_i + a_j +

@@ -42,11 +42,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait (about 2^32 cycles, ~2 s): false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: false once `limit` cycles have passed (default 2^32 cycles, ~2 s).
+constexpr long long kWaitLimitDefault = 1LL << 32;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitLimitDefault) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 32)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -304,7 +306,7 @@ constexpr int TC_NS = 4;          // pipeline stages for column tiles
 static_assert(TC_NS % 2 == 0, "a stage must always hold tiles of one parity");
 
 struct TcShared {
-    uint64_t a_full, a_empty, s_full[TC_NS], s_empty[TC_NS], t_full[2], t_empty[2];
+    uint64_t a_full, a_empty, s_full[TC_NS], s_empty[TC_NS], t_full[2], t_empty[2], drain;
     uint32_t tbase;
     int abort;
 };
@@ -317,7 +319,8 @@ template <int NRHS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
           int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
-          int tiles_per_split, double* __restrict__ part, int* __restrict__ err) {
+          int tiles_per_split, double* __restrict__ part, int* __restrict__ err,
+          long long wlimit, int stall_copies) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzle atoms need 1024-byte alignment; the launch adds 1 KB of slack for this
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -339,6 +342,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             mbar_init(&sh->t_full[b], 1);
             mbar_init(&sh->t_empty[b], TC_EPI_WARPS / 2);
         }
+        mbar_init(&sh->drain, 1);
         sh->abort = 0;
         fence_mbar_init();
     }
@@ -360,24 +364,38 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             uint32_t g = 0, ic = 0;
-            for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
+            // stall_copies (failure-detection tests only): issue nothing, so that every
+            // consumer's bounded wait runs out with no copy or MMA in flight
+            for (int item = blockIdx.x; item < items && !*abort && !stall_copies; item += gridDim.x) {
                 const int rb = item / splits, sp = item - rb * splits;
                 const int t0 = sp * tiles_per_split;
                 const int t1 = min(t0 + tiles_per_split, ntiles);
-                if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u)) { give_up(); break; }
+                if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u, wlimit)) { give_up(); break; }
                 mbar_expect_tx(&sh->a_full, 2 * tileA);
                 bulk_g2s(sA, FA + (size_t)rb * 2 * tileA, 2 * tileA, &sh->a_full);
-                for (int t = t0; t < t1; ++t, ++g) {
+                ++ic;
+                bool ok = true;
+                for (int t = t0; t < t1; ++t) {
                     const int s = g % TC_NS;
-                    if (!mbar_wait(&sh->s_empty[s], ((g / TC_NS) & 1u) ^ 1u)) { give_up(); break; }
+                    if (!mbar_wait(&sh->s_empty[s], ((g / TC_NS) & 1u) ^ 1u, wlimit)) { ok = false; break; }
                     mbar_expect_tx(&sh->s_full[s], tileA + vbytes);
                     bulk_g2s(sB + s * tileA, FB + (size_t)t * tileA, tileA, &sh->s_full[s]);
                     float* dV = sV + s * NRHS * TC_BN;
                     for (int q = 0; q < NRHS; ++q)
                         bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u,
                                  &sh->s_full[s]);
+                    ++g;
                 }
+                if (!ok) { give_up(); break; }
             }
+            // Drain: every copy issued lands before the CTA may exit.  Each barrier has
+            // one arrival per phase (this thread's expect_tx), so the phase of the last
+            // copy into it is the newest one and a parity wait on it is exact.
+            for (uint32_t i = 0; i < (g < (uint32_t)TC_NS ? g : (uint32_t)TC_NS); ++i) {
+                const uint32_t gg = g - 1 - i;
+                mbar_wait(&sh->s_full[gg % TC_NS], (gg / TC_NS) & 1u, wlimit);
+            }
+            if (ic > 0) mbar_wait(&sh->a_full, (ic - 1) & 1u, wlimit);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
@@ -385,15 +403,18 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             const uint32_t idesc = idesc_bf16(128, TC_BN);
             const uint32_t a_addr = smem_u32(sA);
             uint32_t g = 0, ic = 0;
+            bool issued = false;
             for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x, ++ic) {
                 const int sp = item % splits;
                 const int t0 = sp * tiles_per_split;
                 const int t1 = min(t0 + tiles_per_split, ntiles);
-                if (!mbar_wait(&sh->a_full, ic & 1u)) { give_up(); break; }
+                if (!mbar_wait(&sh->a_full, ic & 1u, wlimit)) { give_up(); break; }
+                bool ok = true;
                 for (int t = t0; t < t1; ++t, ++g) {
                     const int s = g % TC_NS, b = g & 1;
-                    if (!mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u)) { give_up(); break; }
-                    if (!mbar_wait(&sh->t_empty[b], ((g >> 1) & 1u) ^ 1u)) { give_up(); break; }
+                    if (!mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u, wlimit)) { ok = false; break; }
+                    if (!mbar_wait(&sh->t_empty[b], ((g >> 1) & 1u) ^ 1u, wlimit)) { ok = false; break; }
+                    issued = true;
                     tc_fence_after();
                     const uint32_t b_addr = smem_u32(sB + s * tileA);
                     for (int h = 0; h < 2; ++h) {
@@ -410,6 +431,13 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                     mma_commit(&sh->s_empty[s]);
                     if (t == t1 - 1) mma_commit(&sh->a_empty);
                 }
+                if (!ok) { give_up(); break; }
+            }
+            // Drain: a commit tracks every MMA this thread issued before it, so once the
+            // drain barrier's first phase completes no MMA still writes TMEM.
+            if (issued) {
+                mma_commit(&sh->drain);
+                mbar_wait(&sh->drain, 0, wlimit);
             }
         }
     } else {
@@ -440,7 +468,8 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             for (int t = t0; t < t1; ++t, ++g) {
                 if ((int)(g & 1u) != par) continue;
                 const int s = g % TC_NS, b = par;
-                ok = mbar_wait(&sh->t_full[b], (g >> 1) & 1u) && mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u);
+                ok = mbar_wait(&sh->t_full[b], (g >> 1) & 1u, wlimit) &&
+                     mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u, wlimit);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) { if (lane == 0) give_up(); break; }
                 tc_fence_after();
@@ -519,14 +548,10 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             }
         }
     }
+    // the producer and the MMA issuer drained their own copies and MMAs above
     __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (*abort) {
-        // bounded drain of MMAs that may still be in flight before the TMEM goes away
-        mbar_wait(&sh->t_full[0], 0);
-        mbar_wait(&sh->t_full[1], 0);
-    }
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
@@ -783,7 +808,7 @@ size_t tc_feature_bytes(long long n, int d) {
 }
 
 typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
-                      int, int, int, double*, int*);
+                      int, int, int, double*, int*, long long, int);
 
 
 // Q = K(rows, cols) V + beta V using features FA (rows) and FB (cols).
@@ -792,9 +817,10 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
     if (kernel_dim(d) > 16) return fail(ctx, KRR_E_INVAL, "tensor-core product needs d <= 16");
     const int Kp = tc_feature_kp(d);
     const int ncp = (int)((nc + TC_BN - 1) / TC_BN * TC_BN);
+    // the error word is cleared by the caller (once per call or solve), so that a timeout
+    // in any product stays visible until the caller reads it
     int* err;
     KRR_RET(bufT(ctx, "tc_err", 1, &err));
-    KRR_TRY_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
     int done = 0;
     while (done < nrhs) {
         const int left = nrhs - done;
@@ -832,8 +858,11 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         double* part;
         KRR_RET(bufT(ctx, "tc_part", (size_t)2 * splits * chunk * nr, &part));
         const int grid = std::min(items, ctx->num_sms);
+        const long long wlimit = ctx->opts.wait_limit_log2 > 0 ? (1LL << ctx->opts.wait_limit_log2)
+                                                               : kWaitLimitDefault;
         fn<<<grid, TC_THREADS, smem_launch, ctx->stream>>>(FA, FB, Kp, (int)nr, (int)nc, ncp, Vp, items,
-                                                           splits, tps, part, err);
+                                                           splits, tps, part, err, wlimit,
+                                                           ctx->opts.test_stall_copies);
         KRR_CHECK_LAUNCH();
         // two column groups per split: 2 * splits partial sums per output
         KRR_RET(launch_kmvm_reduce(ctx, part, 2 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,

@@ -10,7 +10,7 @@ float32; the float32 values are what both sides receive (the oracle upcasts
 them back to float64), so the two see bit-identical data.
 
 Kernel convention: K_ij = exp(-||x_i - x_j||^2 / (2 sigma^2)).  The paper writes
-the Gaussian with a width h and exponent -||x-y||^2/h^2 (Section 2.3, Eq. for the
+the Gaussian with a width h and exponent -||x-y||^2/h^2 (Section 2.4, Eq. for the
 discrete Gauss transform), so h = sqrt(2) * sigma.
 
 Workloads (the paper's datasets are not available; these stand in for them):
@@ -23,6 +23,8 @@ Workloads (the paper's datasets are not available; these stand in for them):
 * ``cube3d``    n=1e6, d=3, X ~ U[0,10]^3, y = sum sin(x_i) + N(0, 0.1^2),
                 sigma=0.8, beta=1e-4, k=2000, 1 or 16 right-hand sides (the
                 extra columns are independent N(0,1)).
+* ``cube3d_density_matched``  the cube shrunk to n points at the same density
+                (side 10 (n/1e6)^(1/3)) and anchors per volume (k = 2000 n/1e6).
 * ``batched``   64 problems, n log-uniform in [1000, 50000], d uniform in
                 {2..16}, X ~ N(0,I), 8 right-hand sides y_j = sin(w_j . x) with
                 w_j ~ N(0,I), sigma=sqrt(d), beta=1e-3, k=min(500, n/10).
@@ -40,7 +42,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Problem", "small", "mixture", "cube3d", "batched", "gradient",
+__all__ = ["Problem", "small", "mixture", "cube3d", "cube3d_density_matched", "batched", "gradient",
            "WORKLOADS", "rademacher_unit"]
 
 
@@ -101,14 +103,27 @@ def mixture(seed: int = 1000, n: int = 100_000, k: int = 1000) -> Problem:
     return Problem("mixture", _f32(X), _f32(y[:, None]), 1.0, 1e-3, min(k, n))
 
 
-def cube3d(seed: int = 2000, n: int = 1_000_000, nrhs: int = 1, k: int = 2000) -> Problem:
+def cube3d(seed: int = 2000, n: int = 1_000_000, nrhs: int = 1, k: int = 2000,
+           side: float = 10.0) -> Problem:
     rng = np.random.Generator(np.random.PCG64(seed))
-    X = rng.uniform(0.0, 10.0, size=(n, 3))
+    X = rng.uniform(0.0, side, size=(n, 3))
     y = np.sin(X).sum(axis=1) + rng.normal(0.0, 0.1, size=n)
     cols = [y]
     for _ in range(nrhs - 1):
         cols.append(rng.normal(0.0, 1.0, size=n))
     return Problem("cube3d", _f32(X), _f32(np.stack(cols, axis=1)), 0.8, 1e-4, min(k, n))
+
+
+def cube3d_density_matched(n: int, seed: int = 2000, nrhs: int = 1) -> Problem:
+    """The cube workload shrunk to n points at the same density (10^6 points per 10^3
+    volume: side 10 (n / 10^6)^(1/3)) and the same anchors per volume (k = 2000 n / 10^6),
+    so the kernel's neighbour counts, its spectrum per unit volume and the preconditioner's
+    coverage match the full-size problem."""
+    side = 10.0 * (n / 1e6) ** (1.0 / 3.0)
+    k = max(1, int(round(2000 * n / 1e6)))
+    p = cube3d(seed=seed, n=n, nrhs=nrhs, k=k, side=side)
+    p.name = "cube3d_density_matched"
+    return p
 
 
 def batched(seed: int = 3000, nprob: int = 64, n_lo: int = 1000, n_hi: int = 50_000,

@@ -132,6 +132,20 @@ def test_kmvm_tensor_core_square(K, n, d, nrhs, beta):
     assert _relcols(Q, ref).max() <= 1e-5
 
 
+def test_kmvm_tensor_core_square_full_size_sampled_rows(K):
+    # the bench workload itself (mixture, n = 10^5, d = 8) in the tensor-core form the
+    # bench times: 256 sampled rows of (K + beta I) V against the oracle, for y and for
+    # an N(0,1) column (the random column cancels more)
+    p = synth.mixture()
+    rng = np.random.Generator(np.random.PCG64(19))
+    V = np.concatenate([p.Y, rng.normal(size=(p.n, 1)).astype(np.float32)], axis=1)
+    ctx = K(precision=1)
+    Q = ctx.kmvm(_t(p.X), _t(p.X), _t(V), p.sigma, p.beta).cpu().numpy()
+    rows = rng.choice(p.n, 256, replace=False)
+    ref = O.kmvm(p.X, V.astype(np.float64), p.sigma, p.beta, rows=rows)
+    assert _relcols(Q[rows], ref).max() <= 1e-5
+
+
 def test_kmvm_tensor_core_rectangular_full_size(K):
     p = synth.mixture()
     rng = np.random.Generator(np.random.PCG64(6))
@@ -248,10 +262,29 @@ def test_precond_apply_matches_oracle_with_shared_anchors(K):
     S = ctx.anchors().cpu().numpy()
     assert len(S) == p.k
     M = O.Nystrom(p.X, S, p.sigma, p.beta)
-    x = np.random.Generator(np.random.PCG64(2)).normal(size=(p.n, 2))
-    z = ctx.apply_precond(_t(x)).cpu().numpy()
+    x = np.random.Generator(np.random.PCG64(2)).normal(size=(p.n, 2)).astype(np.float32)
+    z = ctx.apply_precond(_t(x)).cpu().numpy().astype(np.float64)
     ref = np.stack([M.apply(x[:, 0]), M.apply(x[:, 1])], axis=1)
-    assert _relcols(z, ref).max() <= 2e-3
+    # Backward error.  The GPU stores F = C L1^{-T} in FP32 (kernel values within 4u,
+    # u = 2^-24, L1^{-T} rounded once, k-term FP32 sums) and forms z = (x - F v) / beta
+    # with a k-term FP32 sum and one FP32 subtraction; the k x k solves are FP64.  To first
+    # order z is then the exact Woodbury apply of F^ = F + E with ||E|| <= (k + 5) u ||F||,
+    # perturbed by the F v sum: (K~ + beta I) z - x has norm at most
+    #   eta (||K~|| + beta) ||z||,   eta = (2 (k + 5) + (k + 2)) u,
+    # against the oracle's K~ on the same anchors (Eq. (7)).
+    Kt = M.ktilde()
+    nrmA = np.linalg.norm(Kt, 2) + p.beta
+    k = len(S)
+    eta = (2 * (k + 5) + (k + 2)) * 2.0 ** -24
+    res = Kt @ z + p.beta * z - x
+    back = np.linalg.norm(res, axis=0) / (nrmA * np.linalg.norm(z, axis=0))
+    print(f"apply backward error {back.max():.3e} (bound {eta:.3e})")
+    assert back.max() <= eta
+    # Forward error follows: ||z - z*|| / ||z*|| <= cond(K~ + beta I) eta, with
+    # cond = (||K~|| + beta) / beta (the u ||K~|| / beta scale of an FP32 apply).
+    fwd = _relcols(z, ref).max()
+    print(f"apply forward error {fwd:.3e} (bound {nrmA / p.beta * eta:.3e})")
+    assert fwd <= nrmA / p.beta * eta
 
 
 def test_anchor_quality_close_to_oracle(K):
@@ -269,7 +302,7 @@ def test_anchor_quality_close_to_oracle(K):
 @pytest.mark.parametrize("sparse_r", [0, 8])
 def test_gpu_anchors_meet_the_corollary_condition_bound(K, sparse_r):
     # the anchors the GPU picks (Algorithm 1 or 2) precondition K + beta I below the
-    # Corollary (ID) bound 1 + 2 lambda_{k+1} sqrt(4k(n-k)+1) / beta, and far below
+    # Corollary 4.10 bound 1 + 2 lambda_{k+1} sqrt(4k(n-k)+1) / beta, and far below
     # the unpreconditioned condition number
     p = synth.small(n=800, k=40)
     ctx = K(sparse_r=sparse_r)

@@ -152,3 +152,28 @@ def test_unconverged_solve_returns_its_best_iterate():
     res = np.linalg.norm(O.residual(p.X, a, p.Y, p.sigma, p.beta)) / np.linalg.norm(p.Y)
     assert res <= 1.0
     assert res == pytest.approx(info["rel_residual"][0], rel=1e-6, abs=1e-12)
+
+
+def test_breakdown_discards_the_unverified_correction():
+    # The density-matched cube (the 10^6-point cube's density and anchors per volume at
+    # n = 3 10^4) in the tensor-core form: the expansion's FP32 error is larger than beta
+    # there, so the recurrence can meet non-positive curvature.  On a breakdown the solve
+    # must drop the correction built since the last verified residual and continue in the
+    # exact-difference form from the best verified alpha: whatever the path, the alpha
+    # returned has a verified residual well below alpha = 0's (which is 1), and the
+    # reported residual is that alpha's own (checked on oracle-sampled rows).
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.cube3d_density_matched(30000)
+    ctx = KRR(precision=1, max_iter=1500)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=3)
+    a, info = ctx.solve(_t(p.Y), tol=1e-6, allow_noconv=True)
+    print(f"cube n=3e4: status {info['status']} iters {info['iters']} form {info['product_form']} "
+          f"restarts {info['restarts']} residual {info['rel_residual'][0]:.3e} "
+          f"sweeps {info['sweep_residual']}")
+    assert info["rel_residual"][0] <= 1e-2
+    A = a.cpu().numpy()
+    rows = np.random.Generator(np.random.PCG64(8)).choice(p.n, 200, replace=False)
+    r = p.Y[rows, 0].astype(np.float64) - O.kmvm(p.X, A[:, 0], p.sigma, p.beta, rows=rows)
+    # the sampled residual matches the reported one to within sampling (10x slack)
+    est = np.linalg.norm(r) * np.sqrt(p.n / rows.size) / np.linalg.norm(p.Y[:, 0])
+    assert est <= 10 * info["rel_residual"][0] + 1e-12

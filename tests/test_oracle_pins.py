@@ -196,9 +196,9 @@ def test_nystrom_schur_and_spectrum_bounds():
     Kt = M.ktilde()
     E = K - Kt
     lam = np.linalg.eigvalsh((E + E.T) / 2)
-    assert lam.min() > -1e-10                    # Lemma schur: K - K~ >= 0
+    assert lam.min() > -1e-10                    # Lemma 4.2: K - K~ >= 0
     nrmE = lam.max()
-    mu = O.preconditioned_spectrum(K, Kt, 1e-2)  # Theorem maintheorem proof
+    mu = O.preconditioned_spectrum(K, Kt, 1e-2)  # Theorem 4.5 proof
     assert mu.min() > 1 - 1e-8
     assert mu.max() < 1 + nrmE / 1e-2 + 1e-6
     lk1 = np.linalg.eigvalsh(K)[::-1][len(S)]
@@ -296,7 +296,7 @@ def test_corollary_worked_examples():
 
 
 def test_numerical_rank_helper_matches_corollary_proof():
-    # Eq. condbound_gamma: with delta = beta (xi - 1) / (Mbar n) (taking ||K|| = n), the
+    # Eq. (26): with delta = beta (xi - 1) / (Mbar n) (taking ||K|| = n), the
     # theorem's gamma equals the corollary's, so the two rank formulas agree.
     # (The theorem's bound is used as a formula only: on measured kernels it can be
     # exceeded, e.g. 63 > 49 for 600 points in [0,2]^2, h = 0.707, delta = 1e-6.)
@@ -306,8 +306,64 @@ def test_numerical_rank_helper_matches_corollary_proof():
         assert O.numerical_rank_bound(q, h, delta) == O.tradeoff_rank(q, h, n, beta, xi, Mbar)
 
 
+def test_cond_bound_id_hand_worked_values():
+    # Corollary 4.10: cond <= 1 + 2 lambda_{k+1} sqrt(4k(n-k)+1) / beta, worked by hand.
+    # k=1, n=2, lambda=0.5, beta=1: sqrt(4*1*1+1) = sqrt(5), so 1 + 2*0.5*sqrt(5) = 1 + sqrt(5)
+    assert O.cond_bound_id(0.5, 1, 2, 1.0) == pytest.approx(1.0 + math.sqrt(5.0), rel=1e-15)
+    # k=2, n=4, lambda=0.25, beta=0.5: sqrt(4*2*2+1) = sqrt(17); 1 + 2*0.25*sqrt(17)/0.5
+    assert O.cond_bound_id(0.25, 2, 4, 0.5) == pytest.approx(1.0 + math.sqrt(17.0), rel=1e-15)
+    # k=3, n=10, lambda=1e-3, beta=1e-2: sqrt(4*3*7+1) = sqrt(85) = 9.2195...; 1 + 0.2 sqrt(85)
+    assert O.cond_bound_id(1e-3, 3, 10, 1e-2) == pytest.approx(2.8439088914585776, rel=1e-14)
+    # Remark 4.8: at k = n/2 the factor is sqrt(n^2+1), and the corollary's last line
+    # (sqrt(4k(n-k)+1) <= n+1) bounds every k
+    n, lam, beta = 6, 0.3, 0.7
+    assert O.cond_bound_id(lam, 3, n, beta) == pytest.approx(1 + 2 * lam * math.sqrt(37.0) / beta)
+    for k in range(0, n + 1):
+        assert O.cond_bound_id(lam, k, n, beta) <= 1 + 2 * lam * (n + 1) / beta
+
+
+def test_cond_bound_id_holds_for_two_points():
+    # two points at distance delta: K = [[1, e], [e, 1]], e = exp(-delta^2 / (2 sigma^2)),
+    # eigenvalues 1 + e and 1 - e.  One anchor (the first point) gives K~ = C C^T with
+    # C = (1, e): K~ = [[1, e], [e, e^2]].  det((K + beta I) - mu (K~ + beta I)) factors as
+    # (1 - mu) [(1 + beta)(1 + beta - mu (e^2 + beta)) - e^2 (1 - mu)], so the preconditioned
+    # eigenvalues are 1 and ((1 + beta)^2 - e^2) / (beta (1 + beta + e^2)).
+    sigma, beta = 1.0, 0.1
+    for delta in (0.3, 1.0, 2.5):
+        e = math.exp(-delta * delta / (2 * sigma * sigma))
+        X = np.array([[0.0], [delta]])
+        K = O.kernel_matrix(X, X, sigma)
+        Kt = O.Nystrom(X, np.array([0]), sigma, beta).ktilde()
+        mu = O.preconditioned_spectrum(K, Kt, beta)
+        mu2 = ((1 + beta) ** 2 - e * e) / (beta * (1 + beta + e * e))
+        assert mu.min() == pytest.approx(1.0, rel=1e-12)
+        assert mu.max() == pytest.approx(mu2, rel=1e-12)
+        assert mu.max() / mu.min() <= O.cond_bound_id(1 - e, 1, 2, beta)
+
+
+def test_iteration_estimates_hand_worked_values():
+    # Eq. (31): i = -sqrt(lambda_1) ln(delta) / (2 sqrt(beta)).
+    # lambda_1 = 100, beta = 1, delta = e^-2: -10 * (-2) / 2 = 10
+    assert O.iters_unpreconditioned(100.0, 1.0, math.exp(-2.0)) == pytest.approx(10.0, rel=1e-14)
+    # lambda_1 = 1e4, beta = 1e-2, delta = e^-3: -100 * (-3) / (2 * 0.1) = 1500
+    assert O.iters_unpreconditioned(1e4, 1e-2, math.exp(-3.0)) == pytest.approx(1500.0, rel=1e-14)
+    # Eq. (33): i = ln(delta) / ln((sqrt(beta + M lam) - sqrt(beta)) / (sqrt(beta + M lam) + sqrt(beta))).
+    # M lam = 8, beta = 1: sqrt(9) = 3, ratio (3-1)/(3+1) = 1/2; delta = 2^-10 gives 10
+    assert O.iters_preconditioned(8.0, 1.0, 1.0, 2.0 ** -10) == pytest.approx(10.0, rel=1e-14)
+    # M = 3, lam = 8, beta = 1: sqrt(25) = 5, ratio 4/6 = 2/3; delta = (2/3)^7 gives 7
+    assert O.iters_preconditioned(3.0, 8.0, 1.0, (2.0 / 3.0) ** 7) == pytest.approx(7.0, rel=1e-13)
+    # M lam = 3, beta = 1: sqrt(4) = 2, ratio 1/3; delta = 3^-5 gives 5 (the beta scale
+    # cancels: beta = 4, M lam = 12 gives the same)
+    assert O.iters_preconditioned(1.0, 3.0, 1.0, 3.0 ** -5) == pytest.approx(5.0, rel=1e-13)
+    assert O.iters_preconditioned(2.0, 6.0, 4.0, 3.0 ** -5) == pytest.approx(5.0, rel=1e-13)
+    # Eq. (34)'s small-M-lambda limit: the ratio of Eq. (33) tends to M lam / (4 beta)
+    x = 1e-7
+    assert O.iters_preconditioned(1.0, x, 1.0, 1e-6) == pytest.approx(
+        math.log(1e-6) / math.log(x / 4.0), rel=1e-6)
+
+
 def test_iteration_estimates_are_consistent():
-    # Eq. precond_rate2 with M lambda -> large recovers the unpreconditioned estimate's order
+    # Eq. (33) with M lambda -> large recovers the unpreconditioned estimate's order
     e1 = O.iters_unpreconditioned(1e4, 1e-2, 1e-6)
     e2 = O.iters_preconditioned(1.0, 1e4, 1e-2, 1e-6)
     assert e2 == pytest.approx(e1, rel=0.05)
@@ -385,7 +441,7 @@ def test_sparse_anchors_are_comparable_to_gaussian_ones():
 def test_condition_table_falls_with_k_and_meets_the_corollary():
     # Section 5.1's experiment on a small synthetic set: preconditioning lowers the
     # condition number, more anchors lower it further, and each value sits under the
-    # Corollary (ID) bound
+    # Corollary 4.10 bound
     X = _pts(400, 2, 9, scale=2.0)
     rows = O.condition_table(X, 0.4, 1e-2, (10, 30, 60), seed=1)
     conds = [r["cond"] for r in rows]
@@ -438,7 +494,7 @@ def test_strong_rrqr_meets_its_bounds_on_a_sketch():
 def test_pivoted_qr_of_kernel_sketches_already_meets_strong_rrqr():
     # Section 3's remark (pivoted QR works in practice): on Gaussian kernel sketches the
     # pivoted QR's first k columns already satisfy the strong RRQR conditions with f = 2,
-    # so no swap is needed and the ID bound of Eq. boundid holds for the GPU's pivot rule
+    # so no swap is needed and the ID bound of Eq. (4) holds for the GPU's pivot rule
     for seed, (n, d, sigma, l, k) in enumerate([(120, 2, 0.5, 25, 20), (600, 4, 0.5, 105, 100)]):
         X = np.random.Generator(np.random.PCG64(seed)).uniform(0, 2, size=(n, d))
         A = O.sketch(X, sigma, O.omega(3, l, n)).T
