@@ -19,10 +19,6 @@ import sys
 import tempfile
 import time
 
-os.environ.setdefault("OMP_NUM_THREADS", "1")
-os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-os.environ.setdefault("MKL_NUM_THREADS", "1")
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -103,59 +99,138 @@ def _gpu_index(local_rank: int):
     return local_rank
 
 
-# ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(p, mvm_count: int, budget_s: float = 15.0) -> dict:
-    """Time the FP64 oracle on a bounded sample of the workload's rows and scale it to
-    one solve: n rows x (one sketch row with l columns + mvm_count product rows)."""
+# ------------------------------------------------------------------ CPU oracle baseline
+def _grow(fn, first: int, limit: int, budget_s: float):
+    """Run fn(m) for m = first, 2 first, ... until one call takes budget_s or m reaches
+    limit; return (m, seconds) of the last call."""
+    m = first
+    while True:
+        t0 = time.perf_counter()
+        fn(m)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or m >= limit:
+            return m, dt
+        m = min(limit, 2 * m)
+
+
+def oracle_parts(p, budget_s: float = 3.0) -> dict:
+    """Per-part costs of the FP64 oracle (every host core) on the bench workload:
+    the kernel product (C helper) per row, the Gaussian sketch (Algorithm 1, l columns)
+    per row, pivoted QR of Y^T (dgeqp3) per column on a column sample, the Nystrom
+    factor (Algorithm 3) and one preconditioner apply (Algorithm 4) on n / 8 points."""
     from oracle import krr_oracle as O
+    import scipy.linalg as sla
     rng = np.random.Generator(np.random.PCG64(7))
     X64 = p.X.astype(np.float64)
-    y64 = p.Y.astype(np.float64)
-    Om = O.omega(11, p.l, p.n).T.copy()
-    t_row_mvm = t_row_sk = None
-    rows_done = 0
+    y64 = p.Y[:, 0].astype(np.float64)
+    out = {}
+    m, dt = _grow(lambda m: O.kmvm_c(X64, y64, p.sigma, p.beta, rows=rng.choice(p.n, m, replace=False)),
+                  256, p.n, budget_s)
+    out["product_row_s"], out["product_rows"] = dt / m, m
+    Om = rng.normal(size=(p.n, p.l))        # the sketch's cost does not depend on Omega's values
+    m, dt = _grow(lambda m: O.kmvm_c(X64, Om, p.sigma, 0.0, rows=rng.choice(p.n, m, replace=False)),
+                  8, p.n, budget_s)
+    out["sketch_row_s"], out["sketch_rows"] = dt / m, m
+    del Om
+    m, dt = _grow(lambda m: sla.qr(rng.normal(size=(p.l, m)), mode="r", pivoting=True),
+                  2048, p.n, budget_s)
+    out["qr_col_s"], out["qr_cols"] = dt / m, m
+    # the Nystrom factor and one apply cost O(n k^2) and O(n k): timed on n / 8 points
+    # with the same k, scaled by 8
+    sub = rng.choice(p.n, max(p.k + 1, p.n // 8), replace=False)
+    Xs = X64[sub]
+    S = rng.choice(len(sub), p.k, replace=False)
     t0 = time.perf_counter()
-    nrows = 8
-    while True:
-        rows = rng.choice(p.n, nrows, replace=False)
-        a = time.perf_counter()
-        O.kmvm(X64, y64, p.sigma, p.beta, rows=rows)
-        b = time.perf_counter()
-        O.kmvm_rect(X64[rows], X64, Om, p.sigma)
-        c = time.perf_counter()
-        t_row_mvm = (b - a) / nrows
-        t_row_sk = (c - b) / nrows
-        rows_done += nrows
-        if time.perf_counter() - t0 > budget_s / 3 or nrows >= 256:
-            break
-        nrows *= 2
-    est = p.n * (t_row_sk + mvm_count * t_row_mvm)
-    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"{rows_done} rows of the FP64 oracle product (1 RHS) and of the sketch "
-                       f"(l={p.l} columns) at n={p.n}; scaled to n rows x ({mvm_count} products + "
-                       f"1 sketch); pivoted QR and k x k factorisations not included"),
-            "per_row_product_s": t_row_mvm, "per_row_sketch_s": t_row_sk,
+    M = O.Nystrom(Xs, S, p.sigma, p.beta)
+    out["nystrom_s"] = (time.perf_counter() - t0) * p.n / len(sub)
+    t0 = time.perf_counter()
+    M.apply(y64[sub])
+    out["apply_s"] = (time.perf_counter() - t0) * p.n / len(sub)
+    out["nystrom_points_timed"] = len(sub)
+    del M
+    return out
+
+
+def small_solve_timed() -> dict:
+    """A complete oracle solve of the small workload (n = 2000, d = 4, k = 100): Algorithm 1
+    anchors, Algorithm 3 preconditioner, PCG (Algorithm 5) with a dense FP64 product."""
+    import synth
+    from oracle import krr_oracle as O
+    a = synth.small()
+    t0 = time.perf_counter()
+    alpha, its, _, _ = O.solve_krr(a.X, a.Y[:, 0], a.sigma, a.beta, a.k, seed=1, tol=a.tol)
+    dt = time.perf_counter() - t0
+    res = np.linalg.norm(O.residual(a.X, alpha, a.Y[:, 0], a.sigma, a.beta)) / np.linalg.norm(a.Y)
+    return {"workload": "small n=2000 d=4 sigma=0.5 beta=0.01 k=100 tol=1e-6", "seconds": dt,
+            "iters": its, "rel_residual": float(res)}
+
+
+def oracle_estimate(p, parts: dict, products: int, refinements: int) -> float:
+    """Seconds of one oracle solve of the bench workload: the build (sketch, pivoted QR,
+    Nystrom factor) plus `products` kernel products and preconditioner applies and
+    `refinements` true residuals (each one more product)."""
+    return (p.n * parts["sketch_row_s"] + p.n * parts["qr_col_s"] + parts["nystrom_s"]
+            + products * (p.n * parts["product_row_s"] + parts["apply_s"])
+            + refinements * p.n * parts["product_row_s"])
+
+
+def cpu_baseline(p, products: int, refinements: int, budget_s: float = 3.0) -> dict:
+    from oracle import krr_oracle as O
+    t0 = time.perf_counter()
+    parts = oracle_parts(p, budget_s)
+    small = small_solve_timed()
+    est = oracle_estimate(p, parts, products, refinements)
+    return {"value": est, "unit": "s", "cores": os.cpu_count(), "threads": O.oracle_threads(),
+            "kind": "oracle",
+            "estimate": True,
+            "sample": (f"estimate for one solve of {_describe(p)}: the FP64 oracle's kernel product "
+                       f"(C helper, {O.oracle_threads()} threads) timed on {parts['product_rows']} rows, "
+                       f"its sketch on {parts['sketch_rows']} rows, dgeqp3 on {parts['qr_cols']} columns "
+                       f"of Y^T, the Nystrom factor and one apply on n/8 points; scaled to n rows x "
+                       f"({products} products + {refinements} refinement residuals), the counts of "
+                       f"this run's GPU solve"),
+            "parts": parts, "small_solve_timed": small,
             "elapsed_s": time.perf_counter() - t0}
+
+
+# products per solve of the bench workload and true residuals, as the GPU path's
+# tensor-core form measured them (the reference arm runs without the GPU line)
+REF_PRODUCTS, REF_REFINEMENTS = 780, 3
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import krr_oracle as O
     p = _workload(args.n, 0)
-    mvm_guess = 780   # products of a solve of this workload on the GPU path (tensor-core form)
+    nsteps = args.warmup + args.steps
+    per = max(0.3, min(3.0, 100.0 / max(1, nsteps) / 4))
+    parts0 = oracle_parts(p, per)        # the one-time build parts, measured once
     vals = []
-    for s in range(args.warmup + args.steps):
-        r = oracle_sample(p, mvm_guess, budget_s=min(20.0, 120.0 / max(1, args.warmup + args.steps)))
+    for s in range(nsteps):
+        # each step re-times the per-iteration parts (product rows, one apply) on a sample
+        rng = np.random.Generator(np.random.PCG64(100 + s))
+        X64 = p.X.astype(np.float64)
+        m, dt = _grow(lambda m: O.kmvm_c(X64, p.Y[:, 0].astype(np.float64), p.sigma, p.beta,
+                                         rows=rng.choice(p.n, m, replace=False)), 256, p.n, per)
+        parts = dict(parts0, product_row_s=dt / m, product_rows=m)
         if s >= args.warmup:
-            vals.append(r)
-    v = float(np.mean([r["value"] for r in vals]))
+            vals.append(oracle_estimate(p, parts, REF_PRODUCTS, REF_REFINEMENTS))
+    v = float(np.mean(vals))
+    small = small_solve_timed()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": _describe(p), "l2": "n/a (host)"},
-            "cpu_baseline": {**vals[-1], "value": v},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": os.cpu_count(),
+                             "threads": O.oracle_threads(), "kind": "oracle", "estimate": True,
+                             "sample": (f"per step: the FP64 oracle product (C helper) timed on a row "
+                                        f"sample, plus the build parts timed once (sketch rows, dgeqp3 "
+                                        f"columns, Nystrom factor, one apply); scaled to one solve of "
+                                        f"{REF_PRODUCTS} products and {REF_REFINEMENTS} residuals"),
+                             "parts": parts0, "small_solve_timed": small},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -356,9 +431,15 @@ def run_gpu(args):
                           "h2d_bytes_per_step": int(Xh.numel() * 4 + Yh.numel() * 4),
                           "d2h_bytes_per_step": int(p.n * 8)}
 
+    if out is not None and world == 1 and not args.no_extras:
+        sm_hz = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        out["batched"] = batched_extra(api, sms, sm_hz)
+        out["cube_products"] = cube_extra(api, sms, sm_hz)
+
     if out is not None:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = oracle_sample(p, out["solve"]["mvm_count"])
+            out["cpu_baseline"] = cpu_baseline(p, out["solve"]["mvm_count"], out["solve"]["sweeps"])
         try:
             peaks = {}
             for kind, name in ((0, "ffma_per_s"), (1, "ex2_per_s"), (2, "dfma_per_s")):
@@ -371,6 +452,86 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------ workloads beside the headline
+def _alu_bound(sms: int, sm_hz: float, fma_ops: float) -> float:
+    """Pairs/s bound of a kernel product from its FMA-pipe ops and one ex2 per pair."""
+    return min(sms * 128 * sm_hz / max(fma_ops, 1e-9), sms * 32 * sm_hz)
+
+
+def _form_fma_ops(form: int, d: int, nrhs: int) -> float:
+    """FMA-pipe operations per pair: tensor-core form r FFMA; FP32 expansion d + 1 + r;
+    exact differences 2 d + 2 + r (r right-hand sides)."""
+    return nrhs if form == 1 else (d + 1 + nrhs if form == 0 else 2 * d + 2 + nrhs)
+
+
+def batched_extra(api, sms: int, sm_hz: float, workers: int = 8) -> dict:
+    """The 64-problem batch (n log-uniform in [1e3, 5e4], d in 2..16, 8 RHS) through
+    krr_batch_solve, in the tensor-core form and in the plain FP32 form, each to 1e-6.
+    `frac` = (the batch's products timed at their ALU bounds) / (batch wall time)."""
+    import torch
+    import synth
+    probs = synth.batched()
+    dev = torch.device("cuda")
+    args_ = [(torch.from_numpy(q.X).to(dev), torch.from_numpy(q.Y).to(dev), q.sigma, q.beta, max(1, q.k))
+             for q in probs]
+    out = {"workload": "64 problems, n log-uniform [1e3, 5e4], d in 2..16, X ~ N(0, I), 8 RHS "
+                       "sin(w.x), sigma = sqrt(d), beta = 1e-3, k = min(500, n/10), tol 1e-6",
+           "workers": workers}
+    for prec, name in ((1, "tensor_core"), (0, "fp32")):
+        api.batch_solve(args_[:4], tol=1e-6, seed=1, workers=workers, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, infos, stats = api.batch_solve(args_, tol=1e-6, seed=1, workers=workers, precision=prec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tmin = 0.0
+        pairs = 0.0
+        for q, inf in zip(probs, infos):
+            pp = float(q.n) ** 2 * inf["mvm_count"]
+            pairs += pp
+            form = inf["product_form"]
+            tmin += pp / _alu_bound(sms, sm_hz, _form_fma_ops(form, q.d, q.nrhs))
+        out[name] = {"seconds": dt, "converged": sum(1 for v in stats if v == 0),
+                     "max_rel_residual": max(max(i["rel_residual"]) for i in infos),
+                     "iters_total": sum(i["iters"] for i in infos),
+                     "escalated": sum(1 for i in infos if i["product_form"] == 2),
+                     "product_pairs_per_s": pairs / dt, "frac": tmin / dt,
+                     "frac_basis": "sum over problems of (pairs x products) at the product's ALU "
+                                   "bound for its final form, over the batch wall time"}
+    return out
+
+
+def cube_extra(api, sms: int, sm_hz: float, reps: int = 3) -> dict:
+    """Kernel products of the 10^6-point cube (U[0,10]^3, sigma 0.8, beta 1e-4) for 1 and
+    16 right-hand sides in the tensor-core form and the exact-difference form, timed with
+    CUDA events (mean of `reps` after one warm-up), against each form's ALU bound."""
+    import torch
+    import synth
+    p = synth.cube3d(nrhs=16)
+    X = torch.from_numpy(p.X).cuda()
+    Y = torch.from_numpy(p.Y).cuda()
+    out = {"workload": f"cube n={p.n} d={p.d} sigma={p.sigma:g} beta={p.beta:g}"}
+    for prec in (1, 2):
+        ctx = api.KRR(precision=prec)
+        for nrhs in (1, 16):
+            V = Y[:, :nrhs].contiguous()
+            ctx.kmvm(X, X, V, p.sigma, p.beta)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ctx.kmvm(X, X, V, p.sigma, p.beta)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            rate = float(p.n) ** 2 / (ms / 1e3)
+            bound = _alu_bound(sms, sm_hz, _form_fma_ops(prec, p.d, nrhs))
+            out[f"prec{prec}_nrhs{nrhs}"] = {"ms": ms, "pairs_per_s": rate, "frac": rate / bound,
+                                             "bound_pairs_per_s": bound}
+        ctx.close()
+    return out
 
 
 # ------------------------------------------------------------------ batched workload
@@ -514,6 +675,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-form", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and cube workloads reported beside the headline")
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="kernel product: 0 FP32 tiles, 1 tensor-core tiles (default)")
     ap.add_argument("--workload", default="mixture", choices=["mixture", "batched", "gradient", "cube"])

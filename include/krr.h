@@ -89,6 +89,14 @@ typedef struct krr_opts {
                                  product issue no copies, so its bounded waits run out
                                  (nothing is in flight) and the call returns
                                  KRR_E_TIMEOUT; 0 (default) in all other use             */
+    int    recurrence;    /* PCG vectors: 0 = FP32 x, r, p, z (fastest; enough when
+                             lambda_max(K) / beta is far below 1 / eps32); 1 = FP64 x, r,
+                             p, z, the product fed p as FP32 hi + lo parts with FP64
+                             sums out, and the apply exact for the stored F; 2 (default)
+                             = FP32 until the solve escalates to precision 2, then FP64.
+                             With FP64 vectors the recurrence restarts after every
+                             true-residual replacement                                 */
+    int    reserved[7];
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -106,10 +114,12 @@ typedef struct krr_solve_info {
                                              and after each replacement                */
     int    product_form;                  /* precision of the product at the end (0-2)  */
     int    restarts;                      /* times the CG direction was reset: at an
-                                             escalation, after a stall, or when a true
+                                             escalation, after a stall, when a true
                                              residual came out well above the recursive
-                                             one                                       */
-    int    reserved[5];
+                                             one, or at every replacement with FP64
+                                             vectors                                   */
+    int    recurrence64;                  /* 1 if the solve ended with FP64 vectors     */
+    int    reserved[4];
 } krr_solve_info;
 
 /* Fill *opts with the defaults.  Returns KRR_E_INVAL if opts is NULL. */

@@ -5,7 +5,9 @@ CPU-baseline leg of the benchmark may import this module.  The CUDA path never
 imports, links or calls it, and it shares no code, table or helper with the
 CUDA path; the only common input is the seeded data from ``synth``.
 
-Everything here is plain NumPy / SciPy in float64, written to be checked by eye
+Everything here is plain NumPy / SciPy in float64 (plus one C helper, kmvm64.c, that
+evaluates the kernel product's definition on every host core for the CPU baseline),
+written to be checked by eye
 against the paper (Shabat, Choshen, Ben-Or, Carmel, "Fast and Accurate Gaussian
 Kernel Ridge Regression Using Matrix Decompositions for Preconditioning",
 arXiv 1905.10587).  Library primitives used as single steps: numpy matmul,
@@ -81,6 +83,47 @@ def kmvm(X: np.ndarray, V: np.ndarray, sigma: float, beta: float = 0.0,
     for s in range(0, idx.size, block):
         r = idx[s:s + block]
         out[s:s + len(r)] = kernel_matrix(X[r], X, sigma) @ V2 + beta * V2[r]
+    return out[:, 0] if vec else out
+
+
+_CLIB = None
+
+
+def _clib():
+    """The oracle's C helper (kmvm64.c, FP64, OpenMP over rows), built on first use."""
+    global _CLIB
+    if _CLIB is None:
+        import ctypes as C
+        from . import build_c
+        lib = C.CDLL(build_c.build())
+        lib.oracle_kmvm.restype = None
+        lib.oracle_kmvm.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_int,
+                                    C.c_double, C.c_double, C.c_void_p, C.c_longlong, C.c_void_p]
+        lib.oracle_threads.restype = C.c_int
+        _CLIB = lib
+    return _CLIB
+
+
+def oracle_threads() -> int:
+    """Threads the C helper's OpenMP loops use."""
+    return int(_clib().oracle_threads())
+
+
+def kmvm_c(X: np.ndarray, V: np.ndarray, sigma: float, beta: float = 0.0,
+           rows: np.ndarray | None = None) -> np.ndarray:
+    """(K + beta I) V on ``rows`` (all rows if None): the same definition as ``kmvm``
+    evaluated by the C helper on every host core (FP64, libm exp, index-order sums)."""
+    import ctypes as C
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    vec = V.ndim == 1
+    V2 = np.ascontiguousarray(V[:, None] if vec else V)
+    n, d = X.shape
+    r = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    m = n if r is None else r.size
+    out = np.empty((m, V2.shape[1]))
+    _clib().oracle_kmvm(X.ctypes.data, n, d, V2.ctypes.data, V2.shape[1], float(sigma), float(beta),
+                        None if r is None else r.ctypes.data, m, out.ctypes.data)
     return out[:, 0] if vec else out
 
 

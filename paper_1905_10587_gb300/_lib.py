@@ -27,7 +27,7 @@ class KrrOpts(C.Structure):
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
                 ("escalate", C.c_int), ("sparse_r", C.c_int), ("wait_limit_log2", C.c_int),
-                ("test_stall_copies", C.c_int)]
+                ("test_stall_copies", C.c_int), ("recurrence", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class KrrSolveInfo(C.Structure):
@@ -35,7 +35,7 @@ class KrrSolveInfo(C.Structure):
                 ("rel_residual", C.c_double * KRR_MAX_RHS), ("build_ms", C.c_double),
                 ("solve_ms", C.c_double), ("mvm_count", C.c_int), ("sweep_iters", C.c_int * 8),
                 ("sweep_residual", C.c_double * 8), ("product_form", C.c_int),
-                ("restarts", C.c_int), ("reserved", C.c_int * 5)]
+                ("restarts", C.c_int), ("recurrence64", C.c_int), ("reserved", C.c_int * 4)]
 
 
 _vp, _i, _ll, _d, _ull = C.c_void_p, C.c_int, C.c_longlong, C.c_double, C.c_ulonglong

@@ -219,7 +219,8 @@ class KRR:
                    build_ms=info.build_ms, solve_ms=info.solve_ms, mvm_count=info.mvm_count,
                    sweep_iters=[info.sweep_iters[i] for i in range(min(8, info.sweeps + 1))],
                    sweep_residual=[info.sweep_residual[i] for i in range(min(8, info.sweeps + 1))],
-                   product_form=info.product_form, restarts=info.restarts)
+                   product_form=info.product_form, restarts=info.restarts,
+                   recurrence64=info.recurrence64)
         return _uncols(A, vec), out
 
     def grad(self, y, Xval, yval, tol: float = 1e-8):
@@ -325,7 +326,8 @@ def batch_solve(problems, tol: float = 1e-6, seed: int = 0, workers: int = 8, **
     out = [_uncols(A, vec) for A, vec in alphas]
     info = [dict(status=f.status, iters=f.iters, sweeps=f.sweeps, k_eff=f.k_eff,
                  rel_residual=[f.rel_residual[j] for j in range(nrhs)], solve_ms=f.solve_ms,
-                 build_ms=f.build_ms) for f in infos]
+                 build_ms=f.build_ms, mvm_count=f.mvm_count, product_form=f.product_form)
+            for f in infos]
     return out, info, list(stats)
 
 

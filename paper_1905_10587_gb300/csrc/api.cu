@@ -306,6 +306,7 @@ int krr_default_opts(krr_opts* o) {
     o->pivot_tol = 1e-6;
     o->precision = 0;
     o->escalate = 1;
+    o->recurrence = 2;
     return KRR_OK;
 }
 
@@ -323,6 +324,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         (ctx->opts.wait_limit_log2 != 0 &&
          (ctx->opts.wait_limit_log2 < 10 || ctx->opts.wait_limit_log2 > 40)) ||
         ctx->opts.test_stall_copies < 0 || ctx->opts.test_stall_copies > 1 ||
+        ctx->opts.recurrence < 0 || ctx->opts.recurrence > 2 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -665,6 +667,22 @@ int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out) {
 // recurrence (squared norms compared).
 static constexpr double kGapRestart2 = 4.0;
 
+// (K + beta I) p for FP64 p (n x nrhs): p split into FP32 hi/lo column pairs, FP64 sums out.
+static int square_product64(krr_ctx* ctx, const double* p64, int nrhs, float* psplit, double* q64,
+                            int form) {
+    KRR_RET(launch_split_hilo(ctx, p64, ctx->n, nrhs, psplit));
+    if (form == 1 && ctx->FA)
+        return launch_kmvm_tc(ctx, ctx->FA, ctx->n, ctx->FB, ctx->n, ctx->d, (float)ctx->beta, psplit,
+                              2 * nrhs, nullptr, p64, q64);
+    if (form == 2) {
+        KRR_RET(ensure_raw_points(ctx));
+        return launch_kmvm(ctx, ctx->Praw, ctx->n, ctx->Praw, ctx->n, ctx->d, (float)ctx->beta, psplit,
+                           2 * nrhs, nullptr, (float)(-ctx->s), p64, q64);
+    }
+    return launch_kmvm(ctx, ctx->P, ctx->n, ctx->P, ctx->n, ctx->d, (float)ctx->beta, psplit, 2 * nrhs,
+                       nullptr, 0.f, p64, q64);
+}
+
 int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol, double* alpha,
               krr_solve_info* info) {
     if (!ctx) return KRR_E_INVAL;
@@ -677,8 +695,9 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     const long long n = ctx->n;
     const long long tot = n * nrhs;
     const int nb = cg_vec_blocks(ctx);
+    if (nb != cg64_vec_blocks(ctx)) return fail(ctx, KRR_E_STATE, "vector block counts differ");
     double *r64, *ynorm2, *rnorm2;
-    float *rhs, *x, *r, *z, *p, *q;
+    float *x, *r, *z, *p, *q;
     double *part1, *part2, *part3;
     KRR_RET(bufT(ctx, "sv_r64", (size_t)tot, &r64));
     KRR_RET(bufT(ctx, "sv_yn", (size_t)KRR_MAX_RHS, &ynorm2));
@@ -691,7 +710,23 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     KRR_RET(bufT(ctx, "sv_part1", (size_t)nb * nrhs, &part1));
     KRR_RET(bufT(ctx, "sv_part2", (size_t)nb * nrhs, &part2));
     KRR_RET(bufT(ctx, "sv_part3", (size_t)nb * nrhs, &part3));
-    (void)rhs;
+
+    // FP64 recurrence vectors (opts.recurrence 1, or 2 after an escalation), made on demand
+    bool hp = false;
+    double *x64 = nullptr, *rr64 = nullptr, *z64 = nullptr, *p64 = nullptr, *q64 = nullptr;
+    float* psplit = nullptr;
+    auto enter_hp = [&]() -> int {
+        KRR_RET(bufT(ctx, "sv_x64", (size_t)tot, &x64));
+        KRR_RET(bufT(ctx, "sv_rr64", (size_t)tot, &rr64));
+        KRR_RET(bufT(ctx, "sv_z64", (size_t)tot, &z64));
+        KRR_RET(bufT(ctx, "sv_p64", (size_t)tot, &p64));
+        KRR_RET(bufT(ctx, "sv_q64", (size_t)tot, &q64));
+        KRR_RET(bufT(ctx, "sv_psplit", (size_t)2 * tot, &psplit));
+        KRR_TRY_CUDA(cudaMemsetAsync(x64, 0, sizeof(double) * tot, ctx->stream));
+        hp = true;
+        return KRR_OK;
+    };
+    if (ctx->opts.recurrence == 1) KRR_RET(enter_hp());
 
     std::vector<double> yn(nrhs), rn(nrhs);
     KRR_RET(launch_dot(ctx, Y, Y, n, nrhs, ynorm2));
@@ -708,11 +743,13 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     inf.build_ms = ctx->build_ms;
     int status = KRR_E_NOCONV;
 
-    // One preconditioned CG recurrence in FP32 with reliable updates: whenever the
-    // recursive residual of a column has fallen by the factor opts.inner_tol since the
-    // last true residual (or looks converged), x is folded into the FP64 alpha and the
-    // recursive residual is replaced by y - (K + beta I) alpha evaluated in float-float.
-    // The search direction is kept, so the Krylov space is not thrown away.
+    // One preconditioned CG recurrence with reliable updates: whenever the recursive
+    // residual of a column has fallen by the factor opts.inner_tol since the last true
+    // residual (or looks converged), the correction x is folded into the FP64 alpha and
+    // the recursive residual is replaced by y - (K + beta I) alpha evaluated in
+    // float-float.  With FP32 vectors the search direction is kept, so the Krylov space
+    // is not thrown away; with FP64 vectors (precision-limited problems) the recurrence
+    // restarts from each replaced residual.
     const double delta2 = ctx->opts.inner_tol * ctx->opts.inner_tol;
     std::vector<double> rtrue(nrhs);
     std::vector<int> act(nrhs);
@@ -721,13 +758,19 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     double* abest;
     KRR_RET(bufT(ctx, "sv_abest", (size_t)tot, &abest));
     std::vector<double> best_rel(nrhs, HUGE_VAL);
+    auto zero_x = [&]() -> int {
+        KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+        if (x64) KRR_TRY_CUDA(cudaMemsetAsync(x64, 0, sizeof(double) * tot, ctx->stream));
+        return KRR_OK;
+    };
     auto true_residual = [&](bool first) -> int {
         if (first) {
             KRR_RET(launch_convert_up(ctx, Y, r64, tot));
             for (int c = 0; c < nrhs; ++c) rn[c] = yn[c];
         } else {
             KRR_RET(launch_accumulate(ctx, x, alpha, tot));
-            KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+            if (x64) KRR_RET(launch_add64(ctx, x64, alpha, tot));
+            KRR_RET(zero_x());
             {
                 Phase ph(ctx, PH_RESID);
                 if (ctx->opts.residual == 1)
@@ -758,7 +801,11 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                 KRR_TRY_CUDA(cudaMemcpyAsync(abest + (size_t)c * n, alpha + (size_t)c * n, sizeof(double) * n,
                                              cudaMemcpyDeviceToDevice, ctx->stream));
             }
+        // the recursive residual of either recurrence starts from the true one
         KRR_RET(launch_convert(ctx, r64, r, tot));
+        if (hp)
+            KRR_TRY_CUDA(cudaMemcpyAsync(rr64, r64, sizeof(double) * tot, cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
         return KRR_OK;
     };
     auto any_active = [&]() {
@@ -773,8 +820,19 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     // perturbation is as large as beta I: the FP32 operator then meets non-positive
     // curvature, or stops reducing the true residual, and form 2 takes over.
     int form = ctx->opts.precision == 1 ? (ctx->FA ? 1 : 0) : ctx->opts.precision;
-    // (Re)start the recurrence from the current r: z = M^-1 r, p = z.
+    // (Re)start the recurrence from the current recursive residual: z = M^-1 r, p = z.
     auto restart_cg = [&]() -> int {
+        if (hp) {
+            {
+                Phase ph(ctx, PH_APPLY);
+                KRR_RET(launch_apply_precond64(ctx, rr64, nrhs, z64, part1));
+            }
+            KRR_RET(launch_cg64_start(ctx, rr64, nrhs, part1, part2));
+            KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
+            KRR_TRY_CUDA(cudaMemcpyAsync(p64, z64, sizeof(double) * tot, cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+            return KRR_OK;
+        }
         {
             Phase ph(ctx, PH_APPLY);
             KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part1));
@@ -784,7 +842,6 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         KRR_TRY_CUDA(cudaMemcpyAsync(p, z, sizeof(float) * tot, cudaMemcpyDeviceToDevice, ctx->stream));
         return KRR_OK;
     };
-
     // error word of the tensor-core product (set when one of its bounded waits ran out);
     // read with the CG scalars, into the pinned tail of the scalar mirror
     int* tc_err_dev = nullptr;
@@ -792,7 +849,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     int* tc_err_host = &ctx->cg_host->tc_err;
     *tc_err_host = 0;
     KRR_TRY_CUDA(cudaMemsetAsync(tc_err_dev, 0, sizeof(int), ctx->stream));
-    KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+    KRR_RET(zero_x());
     KRR_RET(true_residual(true));
     if (!any_active()) {
         status = KRR_OK;
@@ -810,13 +867,21 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         while (true) {
             {
                 Phase ph(ctx, PH_KMVM);
-                KRR_RET(square_product(ctx, p, nrhs, q, form));
+                if (hp)
+                    KRR_RET(square_product64(ctx, p64, nrhs, psplit, q64, form));
+                else
+                    KRR_RET(square_product(ctx, p, nrhs, q, form));
             }
             inf.mvm_count++;
             {
                 Phase ph(ctx, PH_CGVEC);
-                KRR_RET(launch_cg_alpha(ctx, p, q, nrhs, part1));
-                KRR_RET(launch_cg_update_xr(ctx, x, r, p, q, nrhs, part2, 0.0));
+                if (hp) {
+                    KRR_RET(launch_cg64_alpha(ctx, p64, q64, nrhs, part1));
+                    KRR_RET(launch_cg64_update_xr(ctx, x64, rr64, p64, q64, nrhs, part2));
+                } else {
+                    KRR_RET(launch_cg_alpha(ctx, p, q, nrhs, part1));
+                    KRR_RET(launch_cg_update_xr(ctx, x, r, p, q, nrhs, part2, 0.0));
+                }
             }
             ++it;
             ++since;
@@ -844,7 +909,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                     // definite in FP32: it is unverified and is discarded, and the solve
                     // goes on from the best verified alpha of every column.
                     escalate = true;
-                    KRR_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * tot, ctx->stream));
+                    KRR_RET(zero_x());
                     KRR_TRY_CUDA(cudaMemcpyAsync(alpha, abest, sizeof(double) * tot,
                                                  cudaMemcpyDeviceToDevice, ctx->stream));
                 }
@@ -870,13 +935,14 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                     // A true residual well above the recursive one means the FP32 operator,
                     // not rounding in the recurrence, set the gap: the old direction is then
                     // no longer conjugate for this residual, so the recurrence restarts.
-                    bool restart = escalate;
+                    // FP64 vectors restart at every replacement.
+                    bool restart = escalate || hp;
                     for (int c = 0; c < nrhs; ++c)
                         if (was[c] && act[c] && !escalate && rtrue[c] > kGapRestart2 * rec[c])
                             restart = true;
                     // two gapped replacements in a row, or a stall: the product's own error,
                     // not the recurrence, limits the solve; move to the exact-difference form
-                    gapped = restart ? gapped + 1 : 0;
+                    gapped = restart && !hp ? gapped + 1 : 0;
                     double w = 0.0;
                     for (int c = 0; c < nrhs; ++c) w = std::max(w, inf.rel_residual[c]);
                     if (w < 0.5 * best) {
@@ -890,6 +956,12 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                         gapped = 0;
                         it_best = it;
                         best = w;
+                        if (ctx->opts.recurrence == 2 && !hp) {
+                            // FP64 vectors from here on, starting from the true residual
+                            KRR_RET(enter_hp());
+                            KRR_TRY_CUDA(cudaMemcpyAsync(rr64, r64, sizeof(double) * tot,
+                                                         cudaMemcpyDeviceToDevice, ctx->stream));
+                        }
                     } else if (stalled) {
                         restart = true;   // already exact differences: fresh direction
                         it_best = it;
@@ -905,11 +977,17 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             }
             {
                 Phase ph(ctx, PH_APPLY);
-                KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part3));
+                if (hp)
+                    KRR_RET(launch_apply_precond64(ctx, rr64, nrhs, z64, part3));
+                else
+                    KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part3));
             }
             {
                 Phase ph(ctx, PH_CGVEC);
-                KRR_RET(launch_cg_beta_p(ctx, p, z, nrhs, part3));
+                if (hp)
+                    KRR_RET(launch_cg64_beta_p(ctx, p64, z64, nrhs, part3));
+                else
+                    KRR_RET(launch_cg_beta_p(ctx, p, z, nrhs, part3));
             }
         }
         inf.iters = it;
@@ -926,6 +1004,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     inf.status = status;
     inf.product_form = form;
+    inf.recurrence64 = hp ? 1 : 0;
     inf.solve_ms = now_ms() - t0;
     if (info) *info = inf;
     if (status == KRR_E_NOCONV) fail(ctx, status, "tolerance not reached");

@@ -529,6 +529,44 @@ int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const dou
     return KRR_OK;
 }
 
+// pieces used by the FP64 recurrence (cg64.cu)
+int launch_gemv_t_reduce(krr_ctx* ctx, const double* upart, int nblk, int nq, int k, int ldF, double* u) {
+    k_gemv_t_reduce<<<dim3(ceil_div(k, 8), nq), 256, 0, ctx->stream>>>(upart, nblk, nq, k, ldF, u);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_tri_gemv(krr_ctx* ctx, const double* T, int k, const double* x, int nq, bool lower, double* y) {
+    k_tri_gemv<<<k, TG_T, 0, ctx->stream>>>(T, k, x, nq, lower, y);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_dot64_parts(krr_ctx* ctx, const double* A, const double* B, long long n, int nrhs, int nb,
+                       double* part) {
+    k_dot64_part<<<nb, VT, 0, ctx->stream>>>(A, B, n, nrhs, part);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_cg_scalars_init(krr_ctx* ctx, const double* rz_part, const double* rr_part, int nb, int nrhs) {
+    k_cg_init<<<1, 32, 0, ctx->stream>>>(ctx->cg, rz_part, rr_part, nb, nrhs);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_cg_scalars_alpha(krr_ctx* ctx, const double* part, int nb, int nrhs) {
+    k_cg_alpha<<<1, 32 * nrhs, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_cg_scalars_check(krr_ctx* ctx, const double* part, int nb, int nrhs, double tol2) {
+    k_cg_check<<<1, 32 * nrhs, 0, ctx->stream>>>(ctx->cg, part, nb, nrhs, tol2);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+int launch_cg_scalars_beta(krr_ctx* ctx, const double* rz_part, int nb, int nrhs) {
+    k_cg_beta<<<1, 32 * nrhs, 0, ctx->stream>>>(ctx->cg, rz_part, nb, nrhs);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
 int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot) {
     k_f64_to_f32<<<vec_blocks(ctx, tot), VT, 0, ctx->stream>>>(a, b, tot);
     KRR_CHECK_LAUNCH();

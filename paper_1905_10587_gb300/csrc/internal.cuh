@@ -177,8 +177,11 @@ int launch_gather_pack(krr_ctx* ctx, const float* P, int ps, const float* X, int
 // Q = K(Pr, Pc) V + beta V (RHS-major, V: nc x nrhs, Q: nr x nrhs).  raw_nsc = 0: Pr, Pc
 // are packed [xh, a] points (expansion form); raw_nsc = -s: they are the raw coordinates
 // packed with mu = 0 and s = 1 and the exponent is raw_nsc * ||x_i - x_j||^2.
+// With Q64 non-null (split mode): V holds nrhs / 2 FP64 columns as hi/lo FP32 column pairs
+// (2q, 2q + 1), nr == nc, and Q64 = K (V_hi + V_lo) + beta V64 in FP64 (nrhs / 2 columns).
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
-                float beta, const float* V, int nrhs, float* Q, float raw_nsc = 0.f);
+                float beta, const float* V, int nrhs, float* Q, float raw_nsc = 0.f,
+                const double* V64 = nullptr, double* Q64 = nullptr);
 // R = Y - (K + beta I) A in FP64 (Y float, A/R double)
 int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);
@@ -194,7 +197,8 @@ int tc_feature_kp(int d);
 size_t tc_feature_bytes(long long n, int d);
 int launch_tc_features(krr_ctx* ctx, const float* P, long long n, int d, int role, unsigned char* out);
 int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
-                   long long nc, int d, float beta, const float* V, int nrhs, float* Q);
+                   long long nc, int d, float beta, const float* V, int nrhs, float* Q,
+                   const double* V64 = nullptr, double* Q64 = nullptr);
 int launch_sketch_tc(krr_ctx* ctx, const unsigned char* FA, const unsigned char* FB, long long n, int d,
                      const void* Om, int l, int njc_alloc, float* Y, int ldy);
 int launch_omega_bf16_tiled(krr_ctx* ctx, unsigned long long seed, int l, long long n, int nab,
@@ -238,6 +242,16 @@ int launch_add_diag(krr_ctx* ctx, double* A, int k, double v);
 
 // cg.cu
 int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part_out);
+// cg64.cu: FP64 recurrence (split product input, FP64 apply and CG updates)
+int launch_split_hilo(krr_ctx* ctx, const double* a, long long n, int nrhs, float* out);
+int launch_apply_precond64(krr_ctx* ctx, const double* R, int nrhs, double* Z, double* rz_part);
+int cg64_vec_blocks(krr_ctx* ctx);
+int launch_cg64_start(krr_ctx* ctx, const double* r, int nrhs, double* rz_part, double* rr_part);
+int launch_cg64_alpha(krr_ctx* ctx, const double* p, const double* q, int nrhs, double* part);
+int launch_cg64_update_xr(krr_ctx* ctx, double* x, double* r, const double* p, const double* q, int nrhs,
+                          double* part);
+int launch_cg64_beta_p(krr_ctx* ctx, double* p, const double* z, int nrhs, const double* rz_part);
+int launch_add64(krr_ctx* ctx, const double* x, double* y, long long tot);
 int launch_dot(krr_ctx* ctx, const float* A, const float* B, long long n, int nrhs, double* out);
 int launch_dot64(krr_ctx* ctx, const double* A, const double* B, long long n, int nrhs, double* out);
 

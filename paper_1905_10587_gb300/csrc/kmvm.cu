@@ -510,9 +510,15 @@ static int choose_splits(int nblk, int ntiles, int slots) {
 
 int choose_splits_public(int nblk, int ntiles, int slots) { return choose_splits(nblk, ntiles, slots); }
 
+int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, int nrhs2,
+                         const double* V64, double beta, double* Q64);
+
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
-                float beta, const float* V, int nrhs, float* Q, float raw_nsc) {
+                float beta, const float* V, int nrhs, float* Q, float raw_nsc, const double* V64,
+                double* Q64) {
     const bool raw = raw_nsc != 0.f;
+    const bool hp = Q64 != nullptr;   // V holds hi/lo column pairs; FP64 output
+    if (hp && (nrhs % 2 != 0 || !V64)) return fail(ctx, KRR_E_INVAL, "kmvm: bad split product");
     if (nr > 0x7fffffffLL || nc > 0x7fffffffLL)
         return fail(ctx, KRR_E_INVAL, "kmvm: more than 2^31 points");
     const int dk = kernel_dim(d);
@@ -531,15 +537,18 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
         double* part = nullptr;
-        if (splits > 1)
+        if (splits > 1 || hp)
             KRR_RET(bufT(ctx, "kmvm_part", (size_t)splits * chunk * nr, &part));
         dim3 grid(nblk, splits);
         const float* Vc = V + (size_t)done * nc;
-        float* Qc = Q + (size_t)done * nr;
+        float* Qc = hp ? nullptr : Q + (size_t)done * nr;
         fn<<<grid, KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps, beta,
                                                  raw_nsc, Qc, (int)nr, part);
         KRR_CHECK_LAUNCH();
-        if (splits > 1) {
+        if (hp) {
+            KRR_RET(launch_kmvm_reduce64(ctx, part, splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
+                                         (double)beta, Q64 + (size_t)(done / 2) * nr));
+        } else if (splits > 1) {
             const long long tot = nr * chunk;
             k_kmvm_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, splits, (int)nr, chunk,
                                                                         Vc, (int)nc, beta, Qc,

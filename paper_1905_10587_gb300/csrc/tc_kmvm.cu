@@ -812,9 +812,15 @@ typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int,
 
 
 // Q = K(rows, cols) V + beta V using features FA (rows) and FB (cols).
+int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, int nrhs2,
+                         const double* V64, double beta, double* Q64);
+
 int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
-                   long long nc, int d, float beta, const float* V, int nrhs, float* Q) {
+                   long long nc, int d, float beta, const float* V, int nrhs, float* Q,
+                   const double* V64, double* Q64) {
     if (kernel_dim(d) > 16) return fail(ctx, KRR_E_INVAL, "tensor-core product needs d <= 16");
+    const bool hp = Q64 != nullptr;   // V holds hi/lo column pairs; FP64 output
+    if (hp && (nrhs % 2 != 0 || !V64)) return fail(ctx, KRR_E_INVAL, "tensor-core product: bad split");
     const int Kp = tc_feature_kp(d);
     const int ncp = (int)((nc + TC_BN - 1) / TC_BN * TC_BN);
     // the error word is cleared by the caller (once per call or solve), so that a timeout
@@ -865,8 +871,12 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
                                                            ctx->opts.test_stall_copies);
         KRR_CHECK_LAUNCH();
         // two column groups per split: 2 * splits partial sums per output
-        KRR_RET(launch_kmvm_reduce(ctx, part, 2 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
-                                   beta, Q + (size_t)done * nr, (int)nr));
+        if (hp)
+            KRR_RET(launch_kmvm_reduce64(ctx, part, 2 * splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
+                                         (double)beta, Q64 + (size_t)(done / 2) * nr));
+        else
+            KRR_RET(launch_kmvm_reduce(ctx, part, 2 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
+                                       beta, Q + (size_t)done * nr, (int)nr));
         done += chunk;
     }
     return KRR_OK;

@@ -70,6 +70,28 @@ def test_kmvm_brute_force_loops():
     np.testing.assert_allclose(O.kmvm(X, V, sigma, beta), ref, rtol=1e-14, atol=1e-14)
     rows = np.array([5, 0, 3])
     np.testing.assert_allclose(O.kmvm(X, V, sigma, beta, rows=rows), ref[rows], rtol=1e-14)
+    # the C helper (every host core) against the same loops
+    np.testing.assert_allclose(O.kmvm_c(X, V, sigma, beta), ref, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(O.kmvm_c(X, V, sigma, beta, rows=rows), ref[rows], rtol=1e-14)
+    np.testing.assert_allclose(O.kmvm_c(X, V[:, 0], sigma, 0.0), ref[:, 0] - beta * V[:, 0],
+                               rtol=1e-13, atol=1e-14)
+
+
+def test_kmvm_c_helper_is_thread_count_independent():
+    # each output row is summed by one thread in index order: results are bitwise
+    # identical for any thread count (the helper is run in a child with 1 and 3 threads)
+    import subprocess
+    import sys
+    code = ("import sys, numpy as np; sys.path.insert(0, %r); from oracle import krr_oracle as O; "
+            "rng = np.random.Generator(np.random.PCG64(8)); X = rng.normal(size=(600, 4)); "
+            "V = rng.normal(size=(600, 2)); sys.stdout.write(O.kmvm_c(X, V, 0.7, 0.1).tobytes().hex())")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for t in ("1", "3"):
+        env = dict(os.environ, OMP_NUM_THREADS=t)
+        outs.append(subprocess.run([sys.executable, "-c", code % root], env=env, check=True,
+                                   capture_output=True, text=True).stdout)
+    assert outs[0] == outs[1] and len(outs[0]) == 600 * 2 * 16
 
 
 def test_kmvm_rect_brute_force():
