@@ -162,6 +162,13 @@ int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream);
  * Runs on the current device and the given stream (NULL = default stream). */
 int krr_peak_probe(int kind, double* ops_per_s, void* stream);
 
+/* Accuracy probe of the two 2^t evaluations the kernel products use: out[i] = 2^t[i]
+ * (t, out: n device floats) by the hardware approximation (method 0, ex2.approx.ftz)
+ * or by the FMA-pipe polynomial of the accurate split product (method 1: round-to-
+ * integer reduction and a degree-7 Taylor polynomial of e^(f ln 2), |f| <= 1/2).  No
+ * counterpart in the paper: the tests compare both against the exact 2^t. */
+int krr_exp2_probe(const float* t, long long n, int method, float* out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Kernel products (Section 2.4, Eq. (6); Definition 2.1).
  * Q = K(Xr, Xc) V + beta * V[0:nr]   (Q: nr x nrhs, V: nc x nrhs, RHS-major).

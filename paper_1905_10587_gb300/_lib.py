@@ -56,6 +56,7 @@ SIGNATURES = {
     "krr_profile_read": (_i, [_vp, C.c_char_p, C.POINTER(_d), C.POINTER(_ll)]),
     "krr_peak_probe": (_i, [_i, C.POINTER(_d), _vp]),
     "krr_tc_selftest": (_i, [_i, C.POINTER(_i), C.POINTER(C.c_float), _vp]),
+    "krr_exp2_probe": (_i, [_vp, _ll, _i, _vp, _vp]),
     "krr_kmvm": (_i, [_vp, _vp, _ll, _vp, _ll, _i, _d, _d, _vp, _i, _vp]),
     "krr_residual_hp": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _vp, _i, _vp]),
     "krr_residual_ff": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _vp, _i, _vp]),

@@ -676,8 +676,9 @@ static int square_product64(krr_ctx* ctx, const double* p64, int nrhs, float* ps
                               2 * nrhs, nullptr, p64, q64);
     if (form == 2) {
         KRR_RET(ensure_raw_points(ctx));
+        const float nsc = (float)(-ctx->s);
         return launch_kmvm(ctx, ctx->Praw, ctx->n, ctx->Praw, ctx->n, ctx->d, (float)ctx->beta, psplit,
-                           2 * nrhs, nullptr, (float)(-ctx->s), p64, q64);
+                           2 * nrhs, nullptr, nsc, p64, q64, (float)(-ctx->s - (double)nsc));
     }
     return launch_kmvm(ctx, ctx->P, ctx->n, ctx->P, ctx->n, ctx->d, (float)ctx->beta, psplit, 2 * nrhs,
                        nullptr, 0.f, p64, q64);

@@ -149,6 +149,30 @@ __device__ __forceinline__ float ex2f(float x) {
     return y;
 }
 
+// 2^t on the FMA pipe, for the accurate product form: t = m + f with m = round(t)
+// (rounded by adding and subtracting 1.5 * 2^23), |f| <= 1/2 exact, and
+// 2^f = e^(f ln 2) = sum_k (ln 2)^k f^k / k! truncated after k = 7 (the first dropped
+// term is below 0.35^8 / 8! = 5.2e-9 relative), in Horner form; the result is scaled by
+// 2^m through its exponent bits.  Arguments below -125 give 0 (the products use t <= 0,
+// and such terms are below FP32 resolution of any sum they enter).
+__device__ __forceinline__ float exp2_poly(float t) {
+    const float magic = 12582912.0f;
+    const float tm = __fadd_rn(t, magic);
+    const float m = __fsub_rn(tm, magic);
+    const float f = __fsub_rn(t, m);
+    float p = 1.5252733804059838e-05f;          // (ln 2)^7 / 7!
+    p = fmaf(p, f, 1.5403530393381606e-04f);    // (ln 2)^6 / 6!
+    p = fmaf(p, f, 1.3333558146428441e-03f);    // (ln 2)^5 / 5!
+    p = fmaf(p, f, 9.6181291076284770e-03f);    // (ln 2)^4 / 4!
+    p = fmaf(p, f, 5.5504108664821576e-02f);    // (ln 2)^3 / 3!
+    p = fmaf(p, f, 2.4022650695910071e-01f);    // (ln 2)^2 / 2!
+    p = fmaf(p, f, 6.9314718055994531e-01f);    // ln 2
+    p = fmaf(p, f, 1.0f);
+    const int mi = __float_as_int(tm) - __float_as_int(magic);
+    const float r = __int_as_float(__float_as_int(p) + (mi << 23));
+    return t < -125.f ? 0.f : r;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -179,9 +203,11 @@ int launch_gather_pack(krr_ctx* ctx, const float* P, int ps, const float* X, int
 // packed with mu = 0 and s = 1 and the exponent is raw_nsc * ||x_i - x_j||^2.
 // With Q64 non-null (split mode): V holds nrhs / 2 FP64 columns as hi/lo FP32 column pairs
 // (2q, 2q + 1), nr == nc, and Q64 = K (V_hi + V_lo) + beta V64 in FP64 (nrhs / 2 columns).
+// In split mode with raw_nsc != 0 (exact differences), raw_nsc + raw_nsc_lo is -s as a
+// float pair, used by the compensated kernels.
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
                 float beta, const float* V, int nrhs, float* Q, float raw_nsc = 0.f,
-                const double* V64 = nullptr, double* Q64 = nullptr);
+                const double* V64 = nullptr, double* Q64 = nullptr, float raw_nsc_lo = 0.f);
 // R = Y - (K + beta I) A in FP64 (Y float, A/R double)
 int launch_residual_hp(krr_ctx* ctx, const float* X, long long n, int d, double sigma, double beta,
                        const float* Y, const double* A, int nrhs, double* R);

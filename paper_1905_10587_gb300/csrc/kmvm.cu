@@ -269,12 +269,22 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
     return d;
 }
 
-template <int D, int NRHS, int R, bool RAW>
+// COMP (split products of the FP64 recurrence, RAW only): V holds hi/lo column pairs;
+// each even (hi) column's tile sum is compensated: the products e v are formed exactly
+// (FMA two-product) and summed with Kahan's compensation, so a tile sum carries an error
+// of a few u |sum| instead of u times the sum of |terms| (strong cancellation across a
+// tile when the direction oscillates).  The odd (lo) columns, 2^-24 smaller, are summed
+// plainly.  The entries are made accurate too: t = -s d^2 with s as a float pair (the
+// kernel writes partial sums only, so the `beta` argument carries the low word of -s),
+// and 2^t from the FMA-pipe polynomial exp2_poly instead of the MUFU approximation.
+template <int D, int NRHS, int R, bool RAW, bool COMP = false>
 __global__ void __launch_bounds__(KM_THREADS, 4)
 k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
         const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc,
         float* __restrict__ Q, int ldq, double* __restrict__ part) {
     static_assert(R % 2 == 0, "rows in pairs");
+    static_assert(!COMP || NRHS % 2 == 0, "compensated sums take hi/lo column pairs");
+    constexpr int NC = COMP ? NRHS / 2 : 1;       // compensated (hi) columns
     constexpr int PS = (D + 1 + 3) / 4 * 4;
     constexpr int PS4 = PS / 4;
     constexpr int PH = PS / 2;                     // 128-bit words per column (2 duplicated coords)
@@ -288,7 +298,13 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
     unsigned long long xi[RP][D];
     unsigned long long ai[RP];
     unsigned long long acc[RP][NRHS];   // one column tile, FP32 pairs
+    unsigned long long kc[RP][NC];      // Kahan compensation of the hi columns (COMP)
+    unsigned long long ne[RP][NC];      // sum of the negated product errors (COMP)
     double acc64[R][NRHS];              // tiles folded in FP64
+#pragma unroll
+    for (int pr = 0; pr < RP; ++pr)
+#pragma unroll
+        for (int h = 0; h < NC; ++h) kc[pr][h] = ne[pr][h] = 0ull;
 #pragma unroll
     for (int pr = 0; pr < RP; ++pr) {
         float xv[2][D], av[2];
@@ -311,6 +327,7 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
 #pragma unroll
         for (int q = 0; q < NRHS; ++q) acc64[r][q] = 0.0;
     const unsigned long long nsc2 = f2_pack(nsc, nsc);
+    const unsigned long long nsclo2 = f2_pack(COMP ? beta : 0.f, COMP ? beta : 0.f);
 
     const int ntiles = (nc + KM_BN - 1) / KM_BN;
     const int t0 = blockIdx.y * tiles_per_split;
@@ -339,11 +356,14 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
                 xj[2 * w] = v.x;
                 xj[2 * w + 1] = v.y;
             }
-            unsigned long long vj[NRHS];
+            unsigned long long vj[NRHS], vn[NC];
 #pragma unroll
             for (int q = 0; q < NRHS; ++q) {
                 const float v = sV[j * NRHS + q];
                 vj[q] = f2_pack(v, v);
+                if constexpr (COMP) {
+                    if (q % 2 == 0) vn[q / 2] = f2_pack(-v, -v);
+                }
             }
 #pragma unroll
             for (int pr = 0; pr < RP; ++pr) {
@@ -355,7 +375,7 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
                         const unsigned long long df = f2_sub(xi[pr][c], xj[c]);
                         ss = f2_fma(df, df, ss);
                     }
-                    tt = f2_mul(ss, nsc2);
+                    tt = COMP ? f2_fma(ss, nsc2, f2_mul(ss, nsclo2)) : f2_mul(ss, nsc2);
                 } else {
                     tt = f2_add(ai[pr], xj[D]);
 #pragma unroll
@@ -363,9 +383,25 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
                 }
                 float t0f, t1f;
                 f2_unpack(tt, t0f, t1f);
-                const unsigned long long e = f2_pack(ex2f(t0f), ex2f(t1f));
+                const unsigned long long e = COMP ? f2_pack(exp2_poly(t0f), exp2_poly(t1f))
+                                                  : f2_pack(ex2f(t0f), ex2f(t1f));
 #pragma unroll
-                for (int q = 0; q < NRHS; ++q) acc[pr][q] = f2_fma(e, vj[q], acc[pr][q]);
+                for (int q = 0; q < NRHS; ++q) {
+                    if constexpr (COMP) {
+                        if (q % 2 == 0) {
+                            // t = fl(e v), -(e v - t) exactly; Kahan: y = t - c, s = acc + y,
+                            // c = (s - acc) - y, acc = s
+                            const unsigned long long t = f2_mul(e, vj[q]);
+                            ne[pr][q / 2] = f2_add(ne[pr][q / 2], f2_fma(e, vn[q / 2], t));
+                            const unsigned long long y = f2_sub(t, kc[pr][q / 2]);
+                            const unsigned long long sum = f2_add(acc[pr][q], y);
+                            kc[pr][q / 2] = f2_sub(f2_sub(sum, acc[pr][q]), y);
+                            acc[pr][q] = sum;
+                            continue;
+                        }
+                    }
+                    acc[pr][q] = f2_fma(e, vj[q], acc[pr][q]);
+                }
             }
         }
         __syncthreads();
@@ -375,6 +411,19 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
             for (int q = 0; q < NRHS; ++q) {
                 float lo, hi;
                 f2_unpack(acc[pr][q], lo, hi);
+                if constexpr (COMP) {
+                    if (q % 2 == 0) {
+                        // exact tile sum ~ s - c - (sum of negated product errors)
+                        float clo, chi, elo, ehi;
+                        f2_unpack(kc[pr][q / 2], clo, chi);
+                        f2_unpack(ne[pr][q / 2], elo, ehi);
+                        acc64[2 * pr][q] += ((double)lo - (double)clo) - (double)elo;
+                        acc64[2 * pr + 1][q] += ((double)hi - (double)chi) - (double)ehi;
+                        kc[pr][q / 2] = ne[pr][q / 2] = 0ull;
+                        acc[pr][q] = 0ull;
+                        continue;
+                    }
+                }
                 acc64[2 * pr][q] += (double)lo;
                 acc64[2 * pr + 1][q] += (double)hi;
                 acc[pr][q] = 0ull;
@@ -472,6 +521,35 @@ static kmvm_fn pick(int dk, int nrhs, int* R, bool raw = false) {
     return nullptr;
 }
 
+// Compensated split-product kernels (exact differences, hi/lo column pairs; d <= 24).
+template <int D, int NRHS>
+static kmvm_fn pick_comp2(int* R) {
+    constexpr int RR = kmvm_rows<D, NRHS + NRHS / 2>();   // room for the compensation terms
+    if constexpr (RR % 2 == 0) {
+        *R = RR;
+        return &k_kmvm2<D, NRHS, RR, true, true>;
+    } else {
+        *R = 2;
+        return &k_kmvm2<D, NRHS, 2, true, true>;
+    }
+}
+template <int D>
+static kmvm_fn pick_comp1(int nrhs, int* R) {
+    if (nrhs == 2) return pick_comp2<D, 2>(R);
+    if (nrhs == 4) return pick_comp2<D, 4>(R);
+    return nullptr;
+}
+static kmvm_fn pick_comp(int dk, int nrhs, int* R) {
+    switch (dk) {
+#define KRR_D(v) \
+    case v: return pick_comp1<v>(nrhs, R);
+        KRR_D(1) KRR_D(2) KRR_D(3) KRR_D(4) KRR_D(5) KRR_D(6) KRR_D(7) KRR_D(8)
+        KRR_D(9) KRR_D(10) KRR_D(11) KRR_D(12) KRR_D(13) KRR_D(14) KRR_D(15) KRR_D(16) KRR_D(24)
+#undef KRR_D
+    }
+    return nullptr;
+}
+
 static int occupancy(krr_ctx* ctx, const void* fn, int threads) {
     (void)ctx;
     static std::mutex mu;   // contexts may run on several host threads (batched solves)
@@ -515,19 +593,23 @@ int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, i
 
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
                 float beta, const float* V, int nrhs, float* Q, float raw_nsc, const double* V64,
-                double* Q64) {
+                double* Q64, float raw_nsc_lo) {
     const bool raw = raw_nsc != 0.f;
     const bool hp = Q64 != nullptr;   // V holds hi/lo column pairs; FP64 output
     if (hp && (nrhs % 2 != 0 || !V64)) return fail(ctx, KRR_E_INVAL, "kmvm: bad split product");
     if (nr > 0x7fffffffLL || nc > 0x7fffffffLL)
         return fail(ctx, KRR_E_INVAL, "kmvm: more than 2^31 points");
     const int dk = kernel_dim(d);
+    // split products of the FP64 recurrence in the exact-difference form: compensated
+    // tile sums, two right-hand sides (four hi/lo columns) per launch
+    const bool comp = hp && raw && dk <= 24;
     int done = 0;
     while (done < nrhs) {
         const int left = nrhs - done;
-        const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        const int chunk = comp ? (left >= 4 ? 4 : 2)
+                               : left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
         int R = 4;
-        kmvm_fn fn = pick(dk, chunk, &R, raw);
+        kmvm_fn fn = comp ? pick_comp(dk, chunk, &R) : pick(dk, chunk, &R, raw);
         if (!fn) return fail(ctx, KRR_E_INVAL, "kmvm: unsupported dimension");
         const int rows_per = KM_THREADS * R;
         const int nblk = (int)ceil_div(nr, rows_per);
@@ -542,7 +624,9 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         dim3 grid(nblk, splits);
         const float* Vc = V + (size_t)done * nc;
         float* Qc = hp ? nullptr : Q + (size_t)done * nr;
-        fn<<<grid, KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps, beta,
+        // compensated kernels: -s as a float pair (raw_nsc_lo rides in the beta slot)
+        const float beta_arg = comp ? raw_nsc_lo : beta;
+        fn<<<grid, KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps, beta_arg,
                                                  raw_nsc, Qc, (int)nr, part);
         KRR_CHECK_LAUNCH();
         if (hp) {

@@ -190,22 +190,51 @@ def test_breakdown_discards_the_unverified_correction(prec):
     assert np.linalg.norm(A - ref) / np.linalg.norm(ref) <= 1e-4
 
 
-def test_density_matched_cube_reaches_the_tolerance():
-    # The 10^6-point cube's density and anchors per volume at n = 3 10^4 (side 3.1, k = 60):
-    # the solve reaches 1e-6, checked on oracle-sampled rows.
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_with_fp64_recurrence_vs_dense(prec):
+    # FP64 recurrence vectors (split product input, FP64 apply): three right-hand sides of
+    # the small workload, residual <= 1e-6 by the oracle's FP64 product and alpha within
+    # 1e-4 of the dense solve
     from paper_1905_10587_gb300.api import KRR
-    p = synth.cube3d_density_matched(30000)
-    ctx = KRR(precision=1, max_iter=6000)
-    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=3)
-    a, info = ctx.solve(_t(p.Y), tol=1e-6, allow_noconv=True)
-    print(f"cube n=3e4: status {info['status']} iters {info['iters']} form {info['product_form']} "
-          f"restarts {info['restarts']} residual {info['rel_residual'][0]:.3e} "
-          f"sweeps {info['sweep_residual']}")
-    assert info["status"] == 0 and info["rel_residual"][0] <= 1e-6
+    p = synth.small()
+    rng = np.random.Generator(np.random.PCG64(12))
+    Y = np.concatenate([p.Y, 0.5 * p.Y + 0.1, rng.normal(size=(p.n, 1))], axis=1).astype(np.float32)
+    ctx = KRR(precision=prec, recurrence=1)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=1)
+    a, info = ctx.solve(_t(Y), tol=1e-6)
+    assert info["recurrence64"] == 1
     A = a.cpu().numpy()
-    rows = np.random.Generator(np.random.PCG64(8)).choice(p.n, 200, replace=False)
-    r = p.Y[rows, 0].astype(np.float64) - O.kmvm(p.X, A[:, 0], p.sigma, p.beta, rows=rows)
-    cond = O.kmvm(p.X, np.abs(A[:, 0]), p.sigma, p.beta, rows=rows)
-    bound = (10 * 1e-6 * np.linalg.norm(p.Y[:, 0]) * np.sqrt(rows.size / p.n)
-             + 1e-13 * np.linalg.norm(cond))
-    assert np.linalg.norm(r) <= bound
+    r = O.residual(p.X, A, Y, p.sigma, p.beta)
+    assert np.all(np.linalg.norm(r, axis=0) / np.linalg.norm(Y, axis=0) <= 1e-6)
+    ref = O.solve_dense(p.X, Y.astype(np.float64), p.sigma, p.beta)
+    assert np.all(np.linalg.norm(A - ref, axis=0) / np.linalg.norm(ref, axis=0) <= 1e-4)
+
+
+def test_recurrence_option_is_validated():
+    from paper_1905_10587_gb300.api import KRR, KRRError
+    with pytest.raises(KRRError):
+        KRR(recurrence=3)
+
+
+def test_exp2_paths_against_exact():
+    # the two 2^t evaluations of the products against the exact value: the hardware
+    # approximation (used by the fast forms) within 3 ulp, the FMA-pipe polynomial of the
+    # accurate split product within 1.5 ulp and without the hardware's bias (the mean error
+    # of each over 4 10^6 arguments in [-20, 0] is reported; the polynomial's must be
+    # below 0.05 ulp, since a coherent error of e ulp shifts the whole kernel by e u K)
+    import ctypes as C
+    from paper_1905_10587_gb300 import _lib
+    lib = _lib.load()
+    t = np.random.Generator(np.random.PCG64(1)).uniform(-20, 0, size=4_000_000).astype(np.float32)
+    td = _t(t)
+    ref = np.exp2(t.astype(np.float64))
+    stats = []
+    for method, max_ulp in ((0, 3.0), (1, 1.5)):
+        out = torch.empty_like(td)
+        assert lib.krr_exp2_probe(C.c_void_p(td.data_ptr()), td.numel(), method, C.c_void_p(out.data_ptr()),
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+        ulp = (out.cpu().numpy().astype(np.float64) - ref) / ref / 2.0 ** -24
+        print(f"exp2 method {method}: mean {ulp.mean():+.3f} ulp, max {np.abs(ulp).max():.2f} ulp")
+        assert np.abs(ulp).max() <= max_ulp
+        stats.append(ulp.mean())
+    assert abs(stats[1]) <= 0.05
