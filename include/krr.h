@@ -89,6 +89,8 @@ typedef struct krr_opts {
                                  product issue no copies, so its bounded waits run out
                                  (nothing is in flight) and the call returns
                                  KRR_E_TIMEOUT; 0 (default) in all other use             */
+    int    no_precond;    /* 1: plain CG without the preconditioner (z = r), for the
+                             condition-number experiment of Section 5.1; 0 (default)   */
     int    recurrence;    /* PCG vectors: 0 = FP32 x, r, p, z (fastest; enough when
                              lambda_max(K) / beta is far below 1 / eps32); 1 = FP64 x, r,
                              p, z, the product fed p as FP32 hi + lo parts with FP64
@@ -96,7 +98,7 @@ typedef struct krr_opts {
                              = FP32 until the solve escalates to precision 2, then FP64.
                              With FP64 vectors the recurrence restarts after every
                              true-residual replacement                                 */
-    int    reserved[7];
+    int    reserved[6];
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -119,7 +121,16 @@ typedef struct krr_solve_info {
                                              one, or at every replacement with FP64
                                              vectors                                   */
     int    recurrence64;                  /* 1 if the solve ended with FP64 vectors     */
-    int    reserved[4];
+    int    lanczos_steps;                 /* CG steps behind cond_estimate              */
+    int    reserved[2];
+    double cond_estimate;                 /* condition number of the system PCG saw
+                                             (with the preconditioner: of
+                                             (K~ + beta I)^{-1} (K + beta I), Theorem 4.5;
+                                             with opts.no_precond: of K + beta I), from
+                                             the extreme eigenvalues of the Lanczos
+                                             tridiagonal that column 0's CG coefficients
+                                             define over its first uninterrupted cycle
+                                             (a lower bound that tightens with the steps) */
 } krr_solve_info;
 
 /* Fill *opts with the defaults.  Returns KRR_E_INVAL if opts is NULL. */

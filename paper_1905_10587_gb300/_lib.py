@@ -27,7 +27,8 @@ class KrrOpts(C.Structure):
                 ("check_every", C.c_int), ("inner_tol", C.c_double), ("anchor_rtol", C.c_double),
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
                 ("escalate", C.c_int), ("sparse_r", C.c_int), ("wait_limit_log2", C.c_int),
-                ("test_stall_copies", C.c_int), ("recurrence", C.c_int), ("reserved", C.c_int * 7)]
+                ("test_stall_copies", C.c_int), ("no_precond", C.c_int), ("recurrence", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class KrrSolveInfo(C.Structure):
@@ -35,7 +36,8 @@ class KrrSolveInfo(C.Structure):
                 ("rel_residual", C.c_double * KRR_MAX_RHS), ("build_ms", C.c_double),
                 ("solve_ms", C.c_double), ("mvm_count", C.c_int), ("sweep_iters", C.c_int * 8),
                 ("sweep_residual", C.c_double * 8), ("product_form", C.c_int),
-                ("restarts", C.c_int), ("recurrence64", C.c_int), ("reserved", C.c_int * 4)]
+                ("restarts", C.c_int), ("recurrence64", C.c_int), ("lanczos_steps", C.c_int),
+                ("reserved", C.c_int * 2), ("cond_estimate", C.c_double)]
 
 
 _vp, _i, _ll, _d, _ull = C.c_void_p, C.c_int, C.c_longlong, C.c_double, C.c_ulonglong

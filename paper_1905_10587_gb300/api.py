@@ -220,7 +220,8 @@ class KRR:
                    sweep_iters=[info.sweep_iters[i] for i in range(min(8, info.sweeps + 1))],
                    sweep_residual=[info.sweep_residual[i] for i in range(min(8, info.sweeps + 1))],
                    product_form=info.product_form, restarts=info.restarts,
-                   recurrence64=info.recurrence64)
+                   recurrence64=info.recurrence64, lanczos_steps=info.lanczos_steps,
+                   cond_estimate=info.cond_estimate)
         return _uncols(A, vec), out
 
     def grad(self, y, Xval, yval, tol: float = 1e-8):

@@ -26,7 +26,11 @@ int allow_max_dynamic_smem(krr_ctx* ctx, const void* fn) {
     int dev = 0, optin = 0;
     KRR_TRY_CUDA(cudaGetDevice(&dev));
     KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    KRR_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    // the dynamic allowance is what the opt-in maximum leaves after the static arrays
+    cudaFuncAttributes fa{};
+    KRR_TRY_CUDA(cudaFuncGetAttributes(&fa, fn));
+    KRR_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      optin - (int)fa.sharedSizeBytes));
     done[fn] = 1;
     return KRR_OK;
 }
@@ -98,6 +102,43 @@ int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot);
 int launch_convert_up(krr_ctx* ctx, const float* a, double* b, long long tot);
 int launch_accumulate(krr_ctx* ctx, const float* x, double* y, long long tot);
 int launch_cg_set_active(krr_ctx* ctx, const int* act_host, int nrhs);
+int launch_identity_apply(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part);
+int launch_identity_apply64(krr_ctx* ctx, const double* R, int nrhs, double* Z, double* rz_part);
+
+// Extreme eigenvalues of the symmetric tridiagonal with diagonal d and off-diagonal e
+// (e[j] couples j-1 and j, e[0] unused) by bisection on Sturm counts: the number of
+// negative pivots of the LDL^T factorisation of T - x I is the number of eigenvalues below x.
+static int sturm_below(const std::vector<double>& d, const std::vector<double>& e, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t j = 0; j < d.size(); ++j) {
+        q = (d[j] - x) - (j ? e[j] * e[j] / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+static void tridiag_extremes(const std::vector<double>& d, const std::vector<double>& e, double* lo,
+                             double* hi) {
+    const int m = (int)d.size();
+    double a = HUGE_VAL, b = -HUGE_VAL;   // Gershgorin bracket
+    for (int j = 0; j < m; ++j) {
+        const double r = (j ? std::fabs(e[j]) : 0.0) + (j + 1 < m ? std::fabs(e[j + 1]) : 0.0);
+        a = std::min(a, d[j] - r);
+        b = std::max(b, d[j] + r);
+    }
+    auto kth = [&](int k) {   // the k-th smallest eigenvalue (1-based)
+        double l = a, h = b;
+        for (int it = 0; it < 200 && h - l > 1e-15 * std::max(std::fabs(l), std::fabs(h)); ++it) {
+            const double mid = 0.5 * (l + h);
+            if (sturm_below(d, e, mid) >= k) h = mid;
+            else l = mid;
+        }
+        return 0.5 * (l + h);
+    };
+    *lo = kth(1);
+    *hi = kth(m);
+}
 
 static const double LOG2E = 1.4426950408889634;
 
@@ -325,6 +366,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
          (ctx->opts.wait_limit_log2 < 10 || ctx->opts.wait_limit_log2 > 40)) ||
         ctx->opts.test_stall_copies < 0 || ctx->opts.test_stall_copies > 1 ||
         ctx->opts.recurrence < 0 || ctx->opts.recurrence > 2 ||
+        ctx->opts.no_precond < 0 || ctx->opts.no_precond > 1 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -743,6 +785,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
     inf.k_eff = ctx->k_eff;
     inf.build_ms = ctx->build_ms;
     int status = KRR_E_NOCONV;
+    std::vector<double> lz_alpha, lz_beta;   // CG step lengths and direction updates
 
     // One preconditioned CG recurrence with reliable updates: whenever the recursive
     // residual of a column has fallen by the factor opts.inner_tol since the last true
@@ -826,7 +869,10 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         if (hp) {
             {
                 Phase ph(ctx, PH_APPLY);
-                KRR_RET(launch_apply_precond64(ctx, rr64, nrhs, z64, part1));
+                if (ctx->opts.no_precond)
+                    KRR_RET(launch_identity_apply64(ctx, rr64, nrhs, z64, part1));
+                else
+                    KRR_RET(launch_apply_precond64(ctx, rr64, nrhs, z64, part1));
             }
             KRR_RET(launch_cg64_start(ctx, rr64, nrhs, part1, part2));
             KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
@@ -836,7 +882,10 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         }
         {
             Phase ph(ctx, PH_APPLY);
-            KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part1));
+            if (ctx->opts.no_precond)
+                KRR_RET(launch_identity_apply(ctx, r, nrhs, z, part1));
+            else
+                KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part1));
         }
         KRR_RET(launch_cg_start(ctx, r, z, nrhs, part1, part2));
         KRR_RET(launch_cg_set_active(ctx, act.data(), nrhs));
@@ -865,6 +914,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         int window = 500, it_best = 0;
         double best = 1.0;
         std::vector<double> rec(nrhs);
+        bool lanczos_on = true;
         while (true) {
             {
                 Phase ph(ctx, PH_KMVM);
@@ -899,6 +949,12 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                     fail(ctx, status, "tensor-core product: a bounded wait timed out");
                     break;
                 }
+                // column 0's CG coefficients while its first cycle runs uninterrupted
+                if (lanczos_on && act[0] && ctx->opts.check_every == 1 && !ctx->cg_host->bad &&
+                    ctx->cg_host->a[0] > 0.0 && lz_alpha.size() < 20000) {
+                    lz_alpha.push_back(ctx->cg_host->a[0]);
+                    lz_beta.push_back(ctx->cg_host->b[0]);   // the previous step's beta
+                }
                 bool escalate = false;
                 if (ctx->cg_host->bad) {
                     if (!ctx->opts.escalate || form == 2 || last) {
@@ -922,6 +978,7 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
                     if (rr <= delta2 * rtrue[c] || rr <= 0.25 * tol * tol * yn[c]) update = true;
                 }
                 if (update) {
+                    lanczos_on = false;
                     if (inf.sweeps < 8) inf.sweep_iters[inf.sweeps] = since;
                     if (inf.sweeps == 0) window = std::max(100, 3 * since);
                     inf.sweeps++;
@@ -978,7 +1035,10 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
             }
             {
                 Phase ph(ctx, PH_APPLY);
-                if (hp)
+                if (ctx->opts.no_precond)
+                    KRR_RET(hp ? launch_identity_apply64(ctx, rr64, nrhs, z64, part3)
+                               : launch_identity_apply(ctx, r, nrhs, z, part3));
+                else if (hp)
                     KRR_RET(launch_apply_precond64(ctx, rr64, nrhs, z64, part3));
                 else
                     KRR_RET(launch_apply_precond(ctx, r, nrhs, z, part3));
@@ -1003,6 +1063,25 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         }
     }
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
+    // Lanczos tridiagonal of the CG coefficients (alpha_j, beta_j): diagonal
+    // 1/alpha_0 and 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_{j-1})/alpha_{j-1};
+    // its eigenvalues are Ritz values of the preconditioned operator
+    if (lz_alpha.size() >= 2) {
+        const size_t m = lz_alpha.size();
+        std::vector<double> dg(m), of(m, 0.0);
+        for (size_t j = 0; j < m; ++j) {
+            dg[j] = 1.0 / lz_alpha[j];
+            if (j) {
+                const double bj = lz_beta[j];   // beta_{j-1}, read with alpha_j
+                dg[j] += bj / lz_alpha[j - 1];
+                of[j] = std::sqrt(std::max(bj, 0.0)) / lz_alpha[j - 1];
+            }
+        }
+        double lo = 0.0, hi = 0.0;
+        tridiag_extremes(dg, of, &lo, &hi);
+        inf.lanczos_steps = (int)m;
+        inf.cond_estimate = lo > 0.0 ? hi / lo : HUGE_VAL;
+    }
     inf.status = status;
     inf.product_form = form;
     inf.recurrence64 = hp ? 1 : 0;

@@ -529,6 +529,29 @@ int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const dou
     return KRR_OK;
 }
 
+// The identity in place of the preconditioner (plain CG): Z = R and per-block partial
+// sums of R.R in the layout of launch_apply_precond's rz_part.
+int launch_identity_apply(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part) {
+    const long long n = ctx->n;
+    if (Z != R)
+        KRR_TRY_CUDA(cudaMemcpyAsync(Z, R, sizeof(float) * n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (rz_part) {
+        k_dot_part<<<vec_blocks(ctx, n), VT, 0, ctx->stream>>>(R, R, n, nrhs, rz_part);
+        KRR_CHECK_LAUNCH();
+    }
+    return KRR_OK;
+}
+int launch_identity_apply64(krr_ctx* ctx, const double* R, int nrhs, double* Z, double* rz_part) {
+    const long long n = ctx->n;
+    if (Z != R)
+        KRR_TRY_CUDA(cudaMemcpyAsync(Z, R, sizeof(double) * n * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (rz_part) {
+        k_dot64_part<<<vec_blocks(ctx, n), VT, 0, ctx->stream>>>(R, R, n, nrhs, rz_part);
+        KRR_CHECK_LAUNCH();
+    }
+    return KRR_OK;
+}
+
 // pieces used by the FP64 recurrence (cg64.cu)
 int launch_gemv_t_reduce(krr_ctx* ctx, const double* upart, int nblk, int nq, int k, int ldF, double* u) {
     k_gemv_t_reduce<<<dim3(ceil_div(k, 8), nq), 256, 0, ctx->stream>>>(upart, nblk, nq, k, ldF, u);

@@ -186,8 +186,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
-// Raise a kernel's dynamic shared-memory cap to the device maximum, once per kernel and
-// process.  Setting it per launch to that launch's size races when several host threads
+// Raise a kernel's dynamic shared-memory cap to the device maximum (less the kernel's
+// static shared memory), once per kernel and process.  Setting it per launch to that launch's size races when several host threads
 // launch the same kernel with different sizes (batched solves).
 int allow_max_dynamic_smem(krr_ctx* ctx, const void* fn);
 

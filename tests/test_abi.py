@@ -45,6 +45,7 @@ def test_binding_declares_every_header_symbol():
 def test_struct_layouts_match_header():
     from paper_1905_10587_gb300 import _lib
     assert C.sizeof(_lib.KrrOpts) == 4 * 4 + 8 * 2 + 4 * 2 + 8 + 4 * 4 + 4 * 8
+    assert _lib.KrrSolveInfo.cond_estimate.offset == 288
     assert _lib.KrrOpts.inner_tol.offset == 16
     assert C.sizeof(_lib.KrrSolveInfo) == 16 + 8 * 16 + 16 + 4 + 4 * 8 + 4 + 8 * 8 + 4 * 7 + 4
     assert _lib.KrrSolveInfo.build_ms.offset == 16 + 8 * 16
@@ -64,14 +65,15 @@ def test_c_struct_layout_matches_binding(tmp_path):
         'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(krr_opts), '
         'offsetof(krr_opts, inner_tol), offsetof(krr_opts, residual), sizeof(krr_solve_info), '
         'offsetof(krr_solve_info, sweep_residual), offsetof(krr_solve_info, mvm_count), '
-        'offsetof(krr_opts, recurrence));return 0;}\n')
+        'offsetof(krr_opts, recurrence) + 1000 * offsetof(krr_solve_info, cond_estimate));return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     want = [C.sizeof(_lib.KrrOpts), _lib.KrrOpts.inner_tol.offset, _lib.KrrOpts.residual.offset,
             C.sizeof(_lib.KrrSolveInfo), _lib.KrrSolveInfo.sweep_residual.offset,
-            _lib.KrrSolveInfo.mvm_count.offset, _lib.KrrOpts.recurrence.offset]
+            _lib.KrrSolveInfo.mvm_count.offset,
+            _lib.KrrOpts.recurrence.offset + 1000 * _lib.KrrSolveInfo.cond_estimate.offset]
     assert got == want
 
 

@@ -236,6 +236,26 @@ def test_qrcp_pivots_on_shared_sketch(K):
     assert np.array_equal(piv[:upto], ref_p[:upto])
 
 
+def test_qrcp_pivots_across_panels(K):
+    # three panels of the blocked pivoted QR (l = 100, k = 90) on rows with a decaying
+    # spectrum: the GPU's pivots replayed through the FP64 greedy rule are maximal within
+    # FP32 rounding, |R_jj| match, and agree with the FP64 choice wherever it is clear
+    rng = np.random.Generator(np.random.PCG64(17))
+    l, n, k = 100, 5000, 90
+    Y = (rng.normal(size=(n, l)) @ np.diag(np.logspace(0, -4, l))).astype(np.float32)
+    ctx = K()
+    piv, rd = ctx.qrcp(_t(Y), k)
+    piv, rd = piv.cpu().numpy(), rd.cpu().numpy()
+    got, best = O.qrcp_replay(Y.T.astype(np.float64), piv)
+    tol = 1e-5 * best[0]
+    assert len(set(piv.tolist())) == k
+    assert np.all(got >= best - tol)
+    np.testing.assert_allclose(rd, got, rtol=0, atol=tol)
+    ref_p, _, gap = O.qrcp_greedy(Y.T.astype(np.float64), k)
+    upto = int(np.argmax(gap < 1e-3)) if np.any(gap < 1e-3) else k
+    assert np.array_equal(piv[:upto], ref_p[:upto])
+
+
 def test_qrcp_pivots_distinct_gaps(K):
     # columns with well separated norms along orthogonal directions: a unique order
     rng = np.random.Generator(np.random.PCG64(4))
@@ -314,6 +334,37 @@ def test_gpu_anchors_meet_the_corollary_condition_bound(K, sparse_r):
     cond = mu.max() / mu.min()
     assert cond <= O.cond_bound_id(lam[len(S)], len(S), p.n, p.beta)
     assert cond < 0.1 * (lam[0] + p.beta) / (lam[-1] + p.beta)
+
+
+def test_condition_estimate_from_pcg_coefficients(K):
+    # Section 5.1's quantity from the solve: the extreme Ritz values of the Lanczos
+    # tridiagonal that column 0's CG coefficients define bound the spectrum from inside, so
+    # the estimate is at most the exact condition number (oracle, FP64 generalized
+    # eigenvalues on the same anchors) and, after enough steps, close to it; with
+    # no_precond it estimates cond(K + beta I) itself
+    p = synth.small(n=1000, k=40)
+    ctx = K(inner_tol=1e-6)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k, seed=4)
+    S = ctx.anchors().cpu().numpy()
+    _, info = ctx.solve(_t(p.Y), tol=1e-7)
+    Kf = O.kernel_matrix(p.X, p.X, p.sigma)
+    mu = O.preconditioned_spectrum(Kf, O.Nystrom(p.X, S, p.sigma, p.beta).ktilde(), p.beta)
+    exact = mu.max() / mu.min()
+    print(f"preconditioned: estimate {info['cond_estimate']:.4g} ({info['lanczos_steps']} steps), "
+          f"exact {exact:.4g}")
+    assert info["lanczos_steps"] >= 10
+    assert info["cond_estimate"] <= exact * (1 + 1e-6)
+    assert info["cond_estimate"] >= 0.5 * exact
+    ctx2 = K(no_precond=1, inner_tol=1e-6, max_iter=20000)
+    ctx2.build(_t(p.X), p.sigma, p.beta, p.k, seed=4)
+    _, info2 = ctx2.solve(_t(p.Y), tol=1e-7, allow_noconv=True)
+    lam = np.linalg.eigvalsh(Kf)
+    exact2 = (lam[-1] + p.beta) / (lam[0] + p.beta)
+    print(f"plain CG: estimate {info2['cond_estimate']:.4g} ({info2['lanczos_steps']} steps), "
+          f"exact {exact2:.4g}")
+    assert info2["cond_estimate"] <= exact2 * (1 + 1e-6)
+    assert info2["cond_estimate"] >= 0.1 * exact2
+    assert info2["cond_estimate"] > 10 * info["cond_estimate"]
 
 
 # ------------------------------------------------------------------ Algorithm 5

@@ -238,3 +238,26 @@ def test_exp2_paths_against_exact():
         assert np.abs(ulp).max() <= max_ulp
         stats.append(ulp.mean())
     assert abs(stats[1]) <= 0.05
+
+
+@pytest.mark.parametrize("n,kmul,max_iter", [(12000, 1, 12000), (30000, 4, 6000)])
+def test_density_matched_cube_reaches_the_tolerance(n, kmul, max_iter):
+    # The 10^6-point cube at n points with the same density: lambda_max(K) / beta ~ 8e7, at
+    # the edge of FP32.  With the cube's anchors per volume (k = 2000 n / 10^6) and with 4x
+    # as many (the rank/condition trade-off of Corollary 4.6), the accurate exact-difference
+    # product with FP64 recurrence vectors reaches 1e-6, checked on oracle-sampled rows.
+    from paper_1905_10587_gb300.api import KRR
+    p = synth.cube3d_density_matched(n)
+    ctx = KRR(precision=2, recurrence=1, max_iter=max_iter, refine_max=200)
+    ctx.build(_t(p.X), p.sigma, p.beta, p.k * kmul, seed=3)
+    a, info = ctx.solve(_t(p.Y), tol=1e-6, allow_noconv=True)
+    print(f"cube n={n} k={p.k * kmul}: status {info['status']} iters {info['iters']} "
+          f"residual {info['rel_residual'][0]:.3e}")
+    assert info["status"] == 0 and info["rel_residual"][0] <= 1e-6
+    A = a.cpu().numpy()
+    rows = np.random.Generator(np.random.PCG64(8)).choice(p.n, 200, replace=False)
+    r = p.Y[rows, 0].astype(np.float64) - O.kmvm(p.X, A[:, 0], p.sigma, p.beta, rows=rows)
+    cond = O.kmvm(p.X, np.abs(A[:, 0]), p.sigma, p.beta, rows=rows)
+    bound = (10 * 1e-6 * np.linalg.norm(p.Y[:, 0]) * np.sqrt(rows.size / p.n)
+             + 1e-13 * np.linalg.norm(cond))
+    assert np.linalg.norm(r) <= bound
