@@ -98,7 +98,11 @@ typedef struct krr_opts {
                              = FP32 until the solve escalates to precision 2, then FP64.
                              With FP64 vectors the recurrence restarts after every
                              true-residual replacement                                 */
-    int    reserved[6];
+    int    ex2_correct;   /* 1: scale the kernel sums of the fast product forms (0, 1 and the
+                             plain exact-difference form) by 1 + 0.83 * 2^-24, the mean
+                             low bias of the hardware 2^t approximation for t < -1 (see
+                             krr_exp2_probe; default); 0: uncorrected                     */
+    int    reserved[5];
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -174,10 +178,11 @@ int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream);
 int krr_peak_probe(int kind, double* ops_per_s, void* stream);
 
 /* Accuracy probe of the two 2^t evaluations the kernel products use: out[i] = 2^t[i]
- * (t, out: n device floats) by the hardware approximation (method 0, ex2.approx.ftz)
- * or by the FMA-pipe polynomial of the accurate split product (method 1: round-to-
- * integer reduction and a degree-7 Taylor polynomial of e^(f ln 2), |f| <= 1/2).  No
- * counterpart in the paper: the tests compare both against the exact 2^t. */
+ * (t, out: n device floats) by the hardware approximation (method 0, ex2.approx.ftz),
+ * by the FMA-pipe polynomial of the accurate split product (method 1: round-to-integer
+ * reduction and a degree-7 Taylor polynomial of e^(f ln 2), |f| <= 1/2), or by the
+ * hardware approximation on the reduced argument (method 2: 2^round(t) * ex2(t - round(t))).
+ * No counterpart in the paper: the tests compare them against the exact 2^t. */
 int krr_exp2_probe(const float* t, long long n, int method, float* out, void* stream);
 
 /* ---------------------------------------------------------------------------

@@ -348,6 +348,7 @@ int krr_default_opts(krr_opts* o) {
     o->precision = 0;
     o->escalate = 1;
     o->recurrence = 2;
+    o->ex2_correct = 1;
     return KRR_OK;
 }
 
@@ -367,6 +368,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.test_stall_copies < 0 || ctx->opts.test_stall_copies > 1 ||
         ctx->opts.recurrence < 0 || ctx->opts.recurrence > 2 ||
         ctx->opts.no_precond < 0 || ctx->opts.no_precond > 1 ||
+        ctx->opts.ex2_correct < 0 || ctx->opts.ex2_correct > 1 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -911,7 +913,8 @@ int krr_solve(krr_ctx* ctx, const float* X, const float* Y, int nrhs, double tol
         // worst column's true residual has not halved within a window, the product's
         // error is what limits the solve.  A replacement is forced once per window so
         // that a stalled column is measured even when no column triggers one.
-        int window = 500, it_best = 0;
+        // (plain CG for the condition-number experiment runs its first cycle unforced)
+        int window = ctx->opts.no_precond ? ctx->opts.max_iter : 500, it_best = 0;
         double best = 1.0;
         std::vector<double> rec(nrhs);
         bool lanczos_on = true;

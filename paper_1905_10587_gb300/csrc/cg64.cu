@@ -39,7 +39,8 @@ __global__ void k_split_hilo(const double* __restrict__ a, long long n, int nrhs
 
 // Q64[q][i] = sum over the partials of columns 2q and 2q + 1 + beta V64[q][i]
 __global__ void k_kmvm_reduce64(const double* __restrict__ part, int nparts, int nr, int nrhs2,
-                                const double* __restrict__ V64, double beta, double* __restrict__ Q64) {
+                                const double* __restrict__ V64, double beta, double* __restrict__ Q64,
+                                double ksc) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int nrhs = nrhs2 / 2;
     if (e >= (long long)nr * nrhs) return;
@@ -48,7 +49,7 @@ __global__ void k_kmvm_reduce64(const double* __restrict__ part, int nparts, int
     double s = 0.0;
     for (int sp = 0; sp < nparts; ++sp)
         s += part[((size_t)sp * nrhs2 + 2 * q) * nr + i] + part[((size_t)sp * nrhs2 + 2 * q + 1) * nr + i];
-    Q64[(size_t)q * nr + i] = s + beta * V64[(size_t)q * nr + i];
+    Q64[(size_t)q * nr + i] = ksc * s + beta * V64[(size_t)q * nr + i];
 }
 
 int launch_split_hilo(krr_ctx* ctx, const double* a, long long n, int nrhs, float* out) {
@@ -58,9 +59,10 @@ int launch_split_hilo(krr_ctx* ctx, const double* a, long long n, int nrhs, floa
 }
 
 int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, int nrhs2,
-                         const double* V64, double beta, double* Q64) {
+                         const double* V64, double beta, double* Q64, double ksc) {
     const long long tot = (long long)nr * (nrhs2 / 2);
-    k_kmvm_reduce64<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, nparts, nr, nrhs2, V64, beta, Q64);
+    k_kmvm_reduce64<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, nparts, nr, nrhs2, V64, beta, Q64,
+                                                                 ksc);
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }

@@ -173,6 +173,18 @@ __device__ __forceinline__ float exp2_poly(float t) {
     return t < -125.f ? 0.f : r;
 }
 
+// The hardware approximation on a reduced argument: 2^t = 2^m * 2^f with m = round(t) and
+// f = t - m in [-1/2, 1/2] (exact), the hardware ex2 on f and the power of two through the
+// exponent bits; arguments below -125 give 0.
+__device__ __forceinline__ float ex2_reduced(float t) {
+    const float magic = 12582912.0f;
+    const float tm = __fadd_rn(t, magic);
+    const float f = __fsub_rn(t, __fsub_rn(tm, magic));
+    const int mi = __float_as_int(tm) - __float_as_int(magic);
+    const float r = __int_as_float(__float_as_int(ex2f(f)) + (mi << 23));
+    return t < -125.f ? 0.f : r;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

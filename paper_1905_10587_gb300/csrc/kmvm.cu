@@ -447,24 +447,33 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
     }
 }
 
+// Q = ksc * (sum of the split partials) + beta V; ksc != 1 corrects the kernel sums for the
+// mean bias of the hardware exponential (see ex2_bias_scale).
 __global__ void k_kmvm_reduce(const double* __restrict__ part, int splits, int nr, int nrhs,
                               const float* __restrict__ V, int ldv, float beta,
-                              float* __restrict__ Q, int ldq) {
+                              float* __restrict__ Q, int ldq, double ksc) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)nr * nrhs) return;
     const int q = (int)(e / nr);
     const int i = (int)(e - (long long)q * nr);
     double s = 0.0;
     for (int sp = 0; sp < splits; ++sp) s += part[((size_t)sp * nrhs + q) * nr + i];
+    s *= ksc;
     if (beta != 0.f) s += (double)beta * V[(size_t)q * ldv + i];
     Q[(size_t)q * ldq + i] = (float)s;
+}
+
+double ex2_bias_scale(const krr_ctx* ctx) {
+    // ex2.approx.ftz.f32 returns 2^t about 0.83 ulp low on average for t < -1 (measured on
+    // GB300 by krr_exp2_probe); the products' kernel sums are scaled back by that much
+    return (ctx && ctx->opts.ex2_correct) ? 1.0 + 0.83 * 5.9604644775390625e-08 : 1.0;
 }
 
 int launch_kmvm_reduce(krr_ctx* ctx, const double* part, int splits, int nr, int nrhs, const float* V,
                        int ldv, float beta, float* Q, int ldq) {
     const long long tot = (long long)nr * nrhs;
     k_kmvm_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, splits, nr, nrhs, V, ldv, beta, Q,
-                                                                ldq);
+                                                                ldq, ex2_bias_scale(ctx));
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }
@@ -589,7 +598,7 @@ static int choose_splits(int nblk, int ntiles, int slots) {
 int choose_splits_public(int nblk, int ntiles, int slots) { return choose_splits(nblk, ntiles, slots); }
 
 int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, int nrhs2,
-                         const double* V64, double beta, double* Q64);
+                         const double* V64, double beta, double* Q64, double ksc);
 
 int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc, int d,
                 float beta, const float* V, int nrhs, float* Q, float raw_nsc, const double* V64,
@@ -618,8 +627,9 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         int splits = choose_splits(nblk, ntiles, slots);
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
+        const double ksc = comp ? 1.0 : ex2_bias_scale(ctx);
         double* part = nullptr;
-        if (splits > 1 || hp)
+        if (splits > 1 || hp || ksc != 1.0)
             KRR_RET(bufT(ctx, "kmvm_part", (size_t)splits * chunk * nr, &part));
         dim3 grid(nblk, splits);
         const float* Vc = V + (size_t)done * nc;
@@ -631,12 +641,12 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         KRR_CHECK_LAUNCH();
         if (hp) {
             KRR_RET(launch_kmvm_reduce64(ctx, part, splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
-                                         (double)beta, Q64 + (size_t)(done / 2) * nr));
-        } else if (splits > 1) {
+                                         (double)beta, Q64 + (size_t)(done / 2) * nr, ksc));
+        } else if (part) {
             const long long tot = nr * chunk;
             k_kmvm_reduce<<<ceil_div(tot, 256), 256, 0, ctx->stream>>>(part, splits, (int)nr, chunk,
                                                                         Vc, (int)nc, beta, Qc,
-                                                                        (int)nr);
+                                                                        (int)nr, ksc);
             KRR_CHECK_LAUNCH();
         }
         done += chunk;
@@ -825,7 +835,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
         if (splits > 1)
             k_kmvm_reduce<<<ceil_div(nr * chunk, 256), 256, 0, stream>>>(part, splits, (int)nr, chunk,
                                                                           Vc, (int)nc, (float)beta,
-                                                                          Qc, (int)nr);
+                                                                          Qc, (int)nr, 1.0);
         done += chunk;
     }
     return cudaGetLastError() == cudaSuccess ? KRR_OK : KRR_E_CUDA;

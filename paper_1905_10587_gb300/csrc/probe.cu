@@ -56,12 +56,13 @@ __global__ void __launch_bounds__(PR_THREADS) k_probe_dfma(int iters, double a, 
     if (s == 1234.5) sink[0] = s;
 }
 
-// out[i] = 2^t[i] by the hardware approximation the products use (method 0) or by the
-// FMA-pipe polynomial of the accurate product form (method 1).
+// out[i] = 2^t[i] by the hardware approximation the products use (method 0), the FMA-pipe
+// polynomial of the accurate product form (method 1), or the hardware approximation on the
+// reduced argument t - round(t) (method 2).
 __global__ void k_exp2_probe(const float* __restrict__ t, long long n, int method, float* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[i] = method == 0 ? ex2f(t[i]) : exp2_poly(t[i]);
+    out[i] = method == 0 ? ex2f(t[i]) : method == 1 ? exp2_poly(t[i]) : ex2_reduced(t[i]);
 }
 
 }  // namespace krr
@@ -69,7 +70,7 @@ __global__ void k_exp2_probe(const float* __restrict__ t, long long n, int metho
 using namespace krr;
 
 extern "C" int krr_exp2_probe(const float* t, long long n, int method, float* out, void* stream) {
-    if (!t || !out || n < 1 || method < 0 || method > 1) return KRR_E_INVAL;
+    if (!t || !out || n < 1 || method < 0 || method > 2) return KRR_E_INVAL;
     k_exp2_probe<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(t, n, method, out);
     return cudaGetLastError() == cudaSuccess ? KRR_OK : KRR_E_CUDA;
 }

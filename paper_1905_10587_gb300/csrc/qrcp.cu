@@ -39,7 +39,8 @@ __device__ __forceinline__ long long key_index(unsigned long long k) {
 // residual norms of all rows (FP64 sums) and the key of the first pivot
 __global__ void __launch_bounds__(QR_THREADS)
 k_qr_norms(const float* __restrict__ Y, long long n, int l, int ldy, double* __restrict__ nrm,
-           unsigned long long* __restrict__ key0) {
+           unsigned long long* __restrict__ bkeys) {
+    __shared__ unsigned long long sbest[QR_WARPS];
     const int lane = threadIdx.x & 31;
     const long long w0 = (long long)blockIdx.x * QR_WARPS + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * QR_WARPS;
@@ -54,7 +55,13 @@ k_qr_norms(const float* __restrict__ Y, long long n, int l, int ldy, double* __r
         if (lane == 0) nrm[i] = s;
         best = max(best, pivot_key(s, i));
     }
-    if (lane == 0) atomicMax(key0, best);
+    if (lane == 0) sbest[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < QR_WARPS; ++w) b = max(b, sbest[w]);
+        bkeys[blockIdx.x] = b;
+    }
 }
 
 // Reflector of pivot step m (panel column jm = m - m0), one block: the pivot row's
@@ -65,13 +72,29 @@ k_qr_norms(const float* __restrict__ Y, long long n, int l, int ldy, double* __r
 __global__ void __launch_bounds__(QR_REF_THREADS)
 k_qr_reflector(const float* __restrict__ Y, long long n, int l, int ldy, int m, int jm, const float* __restrict__ C,
                float* __restrict__ Vp, float* __restrict__ tau, float* __restrict__ g,
-               double* __restrict__ nrm, const unsigned long long* __restrict__ keys, int* __restrict__ piv,
-               float* __restrict__ rdiag) {
+               double* __restrict__ nrm, const unsigned long long* __restrict__ bkeys, int nbk,
+               int* __restrict__ piv, float* __restrict__ rdiag) {
     extern __shared__ double zs[];   // l - m
     __shared__ double red[QR_REF_WARPS];
+    __shared__ unsigned long long kred[QR_REF_WARPS];
     __shared__ double s_alpha, s_scale;
     const int L = l - m;
-    const unsigned long long km = keys[m];
+    // the pivot: the largest of the previous pass's per-block keys
+    {
+        unsigned long long b = 0;
+        for (int i = threadIdx.x; i < nbk; i += QR_REF_THREADS) b = max(b, bkeys[i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        if ((threadIdx.x & 31) == 0) kred[threadIdx.x >> 5] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long t = 0;
+            for (int w = 0; w < QR_REF_WARPS; ++w) t = max(t, kred[w]);
+            kred[0] = t;
+        }
+        __syncthreads();
+    }
+    const unsigned long long km = kred[0];
     const long long p = key_index(km);
     if (km == 0 || p < 0 || p >= n) {   // no candidate left (cannot happen for k <= n): stop
         if (threadIdx.x == 0) {
@@ -160,7 +183,7 @@ template <int NPL>
 __global__ void __launch_bounds__(QR_THREADS)
 k_qr_step(const float* __restrict__ Y, long long n, int l, int ldy, int m, int jm, float* __restrict__ C,
           const float* __restrict__ Vp, const float* __restrict__ tau, const float* __restrict__ g,
-          double* __restrict__ nrm, unsigned long long* __restrict__ keys) {
+          double* __restrict__ nrm, unsigned long long* __restrict__ bkeys) {
     __shared__ float vsh[NPL * 32];   // v_m[m:], zero-padded
     __shared__ float gsh[QH_B], vjm[QH_B];
     __shared__ unsigned long long sbest[QR_WARPS];
@@ -208,7 +231,7 @@ k_qr_step(const float* __restrict__ Y, long long n, int l, int ldy, int m, int j
     if (threadIdx.x == 0) {
         unsigned long long b = 0;
         for (int w = 0; w < QR_WARPS; ++w) b = max(b, sbest[w]);
-        if (b) atomicMax(&keys[m + 1], b);
+        bkeys[blockIdx.x] = b;   // reduced by the next reflector (no atomic contention)
     }
 }
 
@@ -231,7 +254,7 @@ static qr_step_fn qr_step_for(int L) {
 // the key of the next pivot.  One warp per row; the panel's reflectors in shared memory.
 __global__ void __launch_bounds__(QR_THREADS)
 k_qr_panel(float* __restrict__ Y, long long n, int l, int ldy, int m1, int nb, const float* __restrict__ C,
-           const float* __restrict__ Vp, double* __restrict__ nrm, unsigned long long* __restrict__ key) {
+           const float* __restrict__ Vp, double* __restrict__ nrm, unsigned long long* __restrict__ bkeys) {
     extern __shared__ float vps[];   // nb x (l - m1)
     __shared__ unsigned long long sbest[QR_WARPS];
     const int L = l - m1;
@@ -272,7 +295,7 @@ k_qr_panel(float* __restrict__ Y, long long n, int l, int ldy, int m1, int nb, c
     if (threadIdx.x == 0) {
         unsigned long long b = 0;
         for (int w = 0; w < QR_WARPS; ++w) b = max(b, sbest[w]);
-        if (b) atomicMax(key, b);
+        bkeys[blockIdx.x] = b;
     }
 }
 
@@ -280,22 +303,22 @@ int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int*
     if (l > 4096) return fail(ctx, KRR_E_INVAL, "qrcp: more than 4096 projections");
     if (n >= 0xffffffffLL) return fail(ctx, KRR_E_INVAL, "qrcp: too many points");
     if (k > l) return fail(ctx, KRR_E_INVAL, "qrcp: more pivots than projections");
+    // enough warps for every row's loads to be in flight within a few waves; every pass
+    // writes one key per block, which the next reflector reduces
+    const int grid = (int)std::min<long long>((long long)ctx->num_sms * 8, ceil_div(n, QR_WARPS));
     double* nrm;
     float *C, *Vp, *tau, *g;
-    unsigned long long* keys;
+    unsigned long long* bkeys;
     KRR_RET(bufT(ctx, "qr_nrm64", (size_t)n, &nrm));
     KRR_RET(bufT(ctx, "qr_c", (size_t)n * QH_B, &C));
     KRR_RET(bufT(ctx, "qr_v", (size_t)QH_B * l, &Vp));
     KRR_RET(bufT(ctx, "qr_tau", (size_t)QH_B, &tau));
     KRR_RET(bufT(ctx, "qr_g", (size_t)QH_B, &g));
-    KRR_RET(bufT(ctx, "qr_keys", (size_t)k + 1, &keys));
-    KRR_TRY_CUDA(cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (k + 1), ctx->stream));
+    KRR_RET(bufT(ctx, "qr_bkeys", (size_t)grid, &bkeys));
     KRR_RET(allow_max_dynamic_smem(ctx, (const void*)k_qr_panel));
-    // enough warps for every row's loads to be in flight within a few waves
-    const int grid = (int)std::min<long long>((long long)ctx->num_sms * 8, ceil_div(n, QR_WARPS));
     // panel width: the panel's reflectors (nb x l floats) must fit 200 KB of shared memory
     const int bmax = std::max(1, std::min(QH_B, (200 * 1024) / (4 * l)));
-    k_qr_norms<<<grid, QR_THREADS, 0, ctx->stream>>>(Y, n, l, ldy, nrm, keys);
+    k_qr_norms<<<grid, QR_THREADS, 0, ctx->stream>>>(Y, n, l, ldy, nrm, bkeys);
     KRR_CHECK_LAUNCH();
     for (int m0 = 0; m0 < k; m0 += bmax) {
         const int nb = std::min(bmax, k - m0);
@@ -303,22 +326,22 @@ int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int*
             const int m = m0 + jm;
             const int L = l - m;
             if (sizeof(double) * L > 48 * 1024) KRR_RET(allow_max_dynamic_smem(ctx, (const void*)k_qr_reflector));
-            k_qr_reflector<<<1, QR_REF_THREADS, sizeof(double) * L, ctx->stream>>>(Y, n, l, ldy, m, jm, C, Vp, tau,
-                                                                             g, nrm, keys, piv, rdiag);
+            k_qr_reflector<<<1, QR_REF_THREADS, sizeof(double) * L, ctx->stream>>>(Y, n, l, ldy, m, jm, C, Vp,
+                                                                                 tau, g, nrm, bkeys, grid,
+                                                                                 piv, rdiag);
             KRR_CHECK_LAUNCH();
             if (m + 1 < k) {
                 qr_step_for(L)<<<grid, QR_THREADS, 0, ctx->stream>>>(Y, n, l, ldy, m, jm, C, Vp, tau, g, nrm,
-                                                                    keys);
+                                                                    bkeys);
                 KRR_CHECK_LAUNCH();
             }
         }
         const int m1 = m0 + nb;
         if (m1 < k) {
             // the panel's updates reach the coordinates beyond it; the exact norms replace
-            // the downdated ones and give the next pivot (its key slot is reset first)
-            KRR_TRY_CUDA(cudaMemsetAsync(keys + m1, 0, sizeof(unsigned long long), ctx->stream));
+            // the downdated ones and give the next pivot
             const size_t smem = sizeof(float) * (size_t)nb * (l - m1);
-            k_qr_panel<<<grid, QR_THREADS, smem, ctx->stream>>>(Y, n, l, ldy, m1, nb, C, Vp, nrm, keys + m1);
+            k_qr_panel<<<grid, QR_THREADS, smem, ctx->stream>>>(Y, n, l, ldy, m1, nb, C, Vp, nrm, bkeys);
             KRR_CHECK_LAUNCH();
         }
     }

@@ -813,7 +813,8 @@ typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int,
 
 // Q = K(rows, cols) V + beta V using features FA (rows) and FB (cols).
 int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, int nrhs2,
-                         const double* V64, double beta, double* Q64);
+                         const double* V64, double beta, double* Q64, double ksc);
+double ex2_bias_scale(const krr_ctx* ctx);
 
 int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
                    long long nc, int d, float beta, const float* V, int nrhs, float* Q,
@@ -873,7 +874,7 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         // two column groups per split: 2 * splits partial sums per output
         if (hp)
             KRR_RET(launch_kmvm_reduce64(ctx, part, 2 * splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
-                                         (double)beta, Q64 + (size_t)(done / 2) * nr));
+                                         (double)beta, Q64 + (size_t)(done / 2) * nr, ex2_bias_scale(ctx)));
         else
             KRR_RET(launch_kmvm_reduce(ctx, part, 2 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
                                        beta, Q + (size_t)done * nr, (int)nr));

@@ -229,7 +229,7 @@ def test_exp2_paths_against_exact():
     td = _t(t)
     ref = np.exp2(t.astype(np.float64))
     stats = []
-    for method, max_ulp in ((0, 3.0), (1, 1.5)):
+    for method, max_ulp in ((0, 3.0), (1, 1.5), (2, 3.0)):
         out = torch.empty_like(td)
         assert lib.krr_exp2_probe(C.c_void_p(td.data_ptr()), td.numel(), method, C.c_void_p(out.data_ptr()),
                                   C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
@@ -238,6 +238,16 @@ def test_exp2_paths_against_exact():
         assert np.abs(ulp).max() <= max_ulp
         stats.append(ulp.mean())
     assert abs(stats[1]) <= 0.05
+    # the fast products scale their kernel sums by 1 + 0.83 u (opts.ex2_correct): that rests
+    # on the hardware approximation's mean error for t < -1 being near -0.83 ulp
+    tt = t[t < -1.0]
+    out = torch.empty(tt.size, device="cuda", dtype=torch.float32)
+    ttd = _t(tt)
+    assert lib.krr_exp2_probe(C.c_void_p(ttd.data_ptr()), ttd.numel(), 0, C.c_void_p(out.data_ptr()),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    bias = ((out.cpu().numpy().astype(np.float64) - np.exp2(tt.astype(np.float64)))
+            / np.exp2(tt.astype(np.float64)) / 2.0 ** -24).mean()
+    assert -1.0 <= bias <= -0.65
 
 
 @pytest.mark.parametrize("n,kmul,max_iter", [(12000, 1, 12000), (30000, 4, 6000)])
