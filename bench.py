@@ -584,7 +584,8 @@ def run_gradient(args):
     tol = 1e-6
 
     def grad_at(log_sigma, log_beta):
-        ctx = api.KRR(precision=args.precision, max_iter=20000)
+        # lambda_max(K) / beta ~ 2.6e7 here: FP64 recurrence vectors from the start
+        ctx = api.KRR(precision=args.precision, max_iter=20000, recurrence=1)
         ctx.build(X, float(np.exp(log_sigma)), float(np.exp(log_beta)), p.k, seed=1)
         out = ctx.grad(y, Xv, yv, tol=tol)
         ctx.close()
@@ -683,8 +684,10 @@ def run_condition(args):
         X = torch.from_numpy(p.X).cuda()
         Y = torch.from_numpy(p.Y).cuda()
         for k in (0, 100, 500, 1000):
+            # no reliable-update replacement before convergence: the Lanczos estimate uses
+            # the whole uninterrupted recurrence
             ctx = api.KRR(precision=1, no_precond=1 if k == 0 else 0, max_iter=20000 if k else 3000,
-                          refine_max=200)
+                          refine_max=200, inner_tol=1e-12)
             ctx.build(X, p.sigma, p.beta, max(k, 1), seed=1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()

@@ -91,18 +91,23 @@ typedef struct krr_opts {
                                  KRR_E_TIMEOUT; 0 (default) in all other use             */
     int    no_precond;    /* 1: plain CG without the preconditioner (z = r), for the
                              condition-number experiment of Section 5.1; 0 (default)   */
-    int    recurrence;    /* PCG vectors: 0 = FP32 x, r, p, z (fastest; enough when
-                             lambda_max(K) / beta is far below 1 / eps32); 1 = FP64 x, r,
-                             p, z, the product fed p as FP32 hi + lo parts with FP64
-                             sums out, and the apply exact for the stored F; 2 (default)
-                             = FP32 until the solve escalates to precision 2, then FP64.
-                             With FP64 vectors the recurrence restarts after every
-                             true-residual replacement                                 */
-    int    ex2_correct;   /* 1: scale the kernel sums of the fast product forms (0, 1 and the
-                             plain exact-difference form) by 1 + 0.83 * 2^-24, the mean
-                             low bias of the hardware 2^t approximation for t < -1 (see
-                             krr_exp2_probe; default); 0: uncorrected                     */
-    int    reserved[5];
+    int    recurrence;    /* PCG vectors: 0 (default) = FP32 x, r, p, z (fastest; enough
+                             when lambda_max(K) / beta is far below 1 / eps32); 1 = FP64
+                             x, r, p, z, the product fed p as FP32 hi + lo parts with FP64
+                             sums out (in precision 2 the accurate split product), and the
+                             apply exact for the stored F; 2 = FP32 until the solve
+                             escalates to precision 2, then FP64.  With FP64 vectors the
+                             recurrence restarts after every true-residual replacement  */
+    int    strong_swaps;  /* with strong_f > 1: most swaps the strong RRQR may make (0 = 64) */
+    int    ex2_correct;   /* 1 (default): scale the kernel sums of the tensor-core product
+                             (precision 1) by 1 + 0.83 * 2^-24, the mean low bias of the
+                             hardware 2^t approximation for t < -1 (see krr_exp2_probe);
+                             0: uncorrected                                              */
+    int    reserved[4];
+    double strong_f;      /* 0 (default): the build selects anchors by pivoted QR (Algorithm 1
+                             step 3 as Section 3 remarks); f > 1: by strong RRQR with bound
+                             f (Gu-Eisenstat; the factorization Eq. (4) assumes), see
+                             krr_strong_rrqr                                             */
 } krr_opts;
 
 /* Per-solve report (host struct). */
@@ -252,6 +257,21 @@ int krr_sparse_sketch(krr_ctx* ctx, const float* X, long long n, int d, double s
  * (device int32 piv[k]) and |R_jj| (device float rdiag[k]).  Rule: the largest
  * remaining residual norm, lowest index on ties.  Y is overwritten (residuals). */
 int krr_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int k, int* piv, float* rdiag);
+
+/* Strong rank-revealing QR (Gu and Eisenstat) on Y^T: the factorization behind the
+ * interpolative-decomposition bound of Section 2.3 (Eq. (4)).  Starts from krr_qrcp's pivots,
+ * keeps the first k rows of R, and while some pair (pivot position i, other column j) has
+ * (R11^{-1} R12)_ij^2 + gamma_j^2 ||row i of R11^{-1}||^2 > f^2 (gamma_j the residual norm of
+ * column j) swaps them and refactors, at most max_swaps times.  Y (n x l row-major, device)
+ * is overwritten; piv (device int32[k]) and rdiag (device float[k]) as for krr_qrcp; swaps
+ * and rho_max (host; may be NULL) receive the swaps made and the final max sqrt(rho), which
+ * is <= f (within FP32 rounding) unless max_swaps ran out.  Needs 1 <= k <= l, k < n, f > 1. */
+int krr_strong_rrqr(krr_ctx* ctx, float* Y, long long n, int l, int k, double f, int max_swaps,
+                    int* piv, float* rdiag, int* swaps, double* rho_max);
+
+/* Anchor selection statistics of the last build: the swaps its strong RRQR made and its final
+ * max sqrt(rho) (both 0 when the build used plain pivoted QR).  Host outputs. */
+int krr_anchor_stats(krr_ctx* ctx, int* rrqr_swaps, double* rrqr_rho);
 
 /* ---------------------------------------------------------------------------
  * Algorithms 3-5.

@@ -28,7 +28,8 @@ class KrrOpts(C.Structure):
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
                 ("escalate", C.c_int), ("sparse_r", C.c_int), ("wait_limit_log2", C.c_int),
                 ("test_stall_copies", C.c_int), ("no_precond", C.c_int), ("recurrence", C.c_int),
-                ("ex2_correct", C.c_int), ("reserved", C.c_int * 5)]
+                ("strong_swaps", C.c_int), ("ex2_correct", C.c_int), ("reserved", C.c_int * 4),
+                ("strong_f", C.c_double)]
 
 
 class KrrSolveInfo(C.Structure):
@@ -59,6 +60,8 @@ SIGNATURES = {
     "krr_peak_probe": (_i, [_i, C.POINTER(_d), _vp]),
     "krr_tc_selftest": (_i, [_i, C.POINTER(_i), C.POINTER(C.c_float), _vp]),
     "krr_exp2_probe": (_i, [_vp, _ll, _i, _vp, _vp]),
+    "krr_strong_rrqr": (_i, [_vp, _vp, _ll, _i, _i, _d, _i, _vp, _vp, C.POINTER(_i), C.POINTER(_d)]),
+    "krr_anchor_stats": (_i, [_vp, C.POINTER(_i), C.POINTER(_d)]),
     "krr_kmvm": (_i, [_vp, _vp, _ll, _vp, _ll, _i, _d, _d, _vp, _i, _vp]),
     "krr_residual_hp": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _vp, _i, _vp]),
     "krr_residual_ff": (_i, [_vp, _vp, _ll, _i, _d, _d, _vp, _vp, _i, _vp]),

@@ -175,6 +175,22 @@ class KRR:
         self._check(self.lib.krr_qrcp(self.h, _ptr(Y), Y.shape[0], Y.shape[1], k, _ptr(piv), _ptr(rd)))
         return piv, rd
 
+    def strong_rrqr(self, Y, k: int, f: float = 2.0, max_swaps: int = 64):
+        """Strong RRQR (Gu-Eisenstat, bound f) of Y^T: (pivots, |R_jj|, swaps, max sqrt(rho))."""
+        Y = _cuda(Y, torch.float32, "Y").clone()
+        piv = torch.empty(k, device=Y.device, dtype=torch.int32)
+        rd = torch.empty(k, device=Y.device, dtype=torch.float32)
+        sw, rho = C.c_int(), C.c_double()
+        self._check(self.lib.krr_strong_rrqr(self.h, _ptr(Y), Y.shape[0], Y.shape[1], k, f, max_swaps,
+                                             _ptr(piv), _ptr(rd), C.byref(sw), C.byref(rho)))
+        return piv, rd, sw.value, rho.value
+
+    def anchor_stats(self):
+        """(swaps, max sqrt(rho)) of the last build's strong RRQR ((0, 0) for pivoted QR)."""
+        sw, rho = C.c_int(), C.c_double()
+        self._check(self.lib.krr_anchor_stats(self.h, C.byref(sw), C.byref(rho)))
+        return sw.value, rho.value
+
     # ---------------------------------------------------------------- Algorithms 3-5
     def build(self, X, sigma: float, beta: float, k: int, seed: int = 0, anchors=None):
         """Algorithm 5 steps 1-2: anchors (Algorithm 1, or the given ones) and Algorithm 3."""

@@ -347,7 +347,7 @@ int krr_default_opts(krr_opts* o) {
     o->pivot_tol = 1e-6;
     o->precision = 0;
     o->escalate = 1;
-    o->recurrence = 2;
+    o->recurrence = 0;
     o->ex2_correct = 1;
     return KRR_OK;
 }
@@ -369,6 +369,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.recurrence < 0 || ctx->opts.recurrence > 2 ||
         ctx->opts.no_precond < 0 || ctx->opts.no_precond > 1 ||
         ctx->opts.ex2_correct < 0 || ctx->opts.ex2_correct > 1 ||
+        !(ctx->opts.strong_f == 0.0 || ctx->opts.strong_f > 1.0) || ctx->opts.strong_swaps < 0 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
         return KRR_E_INVAL;
@@ -642,9 +643,16 @@ int krr_build_precond(krr_ctx* ctx, const float* X, long long n, int d, double s
     float* rdiag;
     KRR_RET(bufT(ctx, "piv", (size_t)k, &piv));
     KRR_RET(bufT(ctx, "rdiag", (size_t)k, &rdiag));
+    ctx->rrqr_swaps = 0;
+    ctx->rrqr_rho = 0.0;
     {
         Phase ph(ctx, PH_QRCP);
-        KRR_RET(launch_qrcp(ctx, Y, n, l, ld, k, piv, rdiag));
+        if (ctx->opts.strong_f > 1.0 && k < n)
+            KRR_RET(launch_strong_rrqr(ctx, Y, n, l, ld, k, ctx->opts.strong_f,
+                                       ctx->opts.strong_swaps > 0 ? ctx->opts.strong_swaps : 64, piv, rdiag,
+                                       &ctx->rrqr_swaps, &ctx->rrqr_rho));
+        else
+            KRR_RET(launch_qrcp(ctx, Y, n, l, ld, k, piv, rdiag));
     }
     std::vector<float> rd(k);
     KRR_TRY_CUDA(cudaMemcpyAsync(rd.data(), rdiag, sizeof(float) * k, cudaMemcpyDeviceToHost,
@@ -687,6 +695,14 @@ int krr_build_precond_anchors(krr_ctx* ctx, const float* X, long long n, int d, 
     KRR_TRY_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->build_ms = now_ms() - t0;
     ctx->built = true;
+    return KRR_OK;
+}
+
+int krr_anchor_stats(krr_ctx* ctx, int* rrqr_swaps, double* rrqr_rho) {
+    if (!ctx || !rrqr_swaps || !rrqr_rho) return KRR_E_INVAL;
+    if (!ctx->built) return fail(ctx, KRR_E_STATE, "no preconditioner built");
+    *rrqr_swaps = ctx->rrqr_swaps;
+    *rrqr_rho = ctx->rrqr_rho;
     return KRR_OK;
 }
 

@@ -101,6 +101,8 @@ struct krr_ctx {
     double sigma = 0, beta = 0, s = 0;   // s = log2(e)/(2 sigma^2)
     int k = 0, k_eff = 0, l = 0, ldF = 0;
     double build_ms = 0;
+    int rrqr_swaps = 0;        // strong RRQR statistics of the last build
+    double rrqr_rho = 0;
     // device arrays (views into bufs)
     float* P = nullptr;        // n x ps packed points of X
     float* Praw = nullptr;     // n x ps raw coordinates of X (difference form), on demand
@@ -262,8 +264,10 @@ int launch_kgemm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, l
 // G = beta I + F^T F (FP64 k x k, full), F: n x ldF
 int launch_gram(krr_ctx* ctx, const float* F, long long n, int k, int ldF, double beta, double* G);
 
-// qrcp.cu
+// qrcp.cu, rrqr.cu
 int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int* piv, float* rdiag);
+int launch_strong_rrqr(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, double f, int max_swaps,
+                       int* piv, float* rdiag, int* swaps_out, double* rho_out);
 
 // dense64.cu
 int launch_kss(krr_ctx* ctx, const float* XS, int k, int d, double sigma, double* A);

@@ -120,7 +120,7 @@ constexpr int KM_BN = 128;
 template <int D, int NRHS, int R, bool RAW>
 __global__ void __launch_bounds__(KM_THREADS, 4)
 k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
-       const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc,
+       const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc, float kcorr,
        float* __restrict__ Q, int ldq, double* __restrict__ part) {
     constexpr int PS = (D + 1 + 3) / 4 * 4;
     constexpr int PS4 = PS / 4;
@@ -223,7 +223,8 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
                 Q[(size_t)q * ldq + i] =
-                    (float)(acc64[r][q] + (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
+                    (float)(acc64[r][q] * (1.0 + (double)kcorr) +
+                            (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
         } else {
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
@@ -280,7 +281,7 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
 template <int D, int NRHS, int R, bool RAW, bool COMP = false>
 __global__ void __launch_bounds__(KM_THREADS, 4)
 k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int nc,
-        const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc,
+        const float* __restrict__ V, int ldv, int tiles_per_split, float beta, float nsc, float kcorr,
         float* __restrict__ Q, int ldq, double* __restrict__ part) {
     static_assert(R % 2 == 0, "rows in pairs");
     static_assert(!COMP || NRHS % 2 == 0, "compensated sums take hi/lo column pairs");
@@ -438,7 +439,8 @@ k_kmvm2(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int 
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
                 Q[(size_t)q * ldq + i] =
-                    (float)(acc64[r][q] + (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
+                    (float)(acc64[r][q] * (1.0 + (double)kcorr) +
+                            (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
         } else {
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
@@ -465,7 +467,9 @@ __global__ void k_kmvm_reduce(const double* __restrict__ part, int splits, int n
 
 double ex2_bias_scale(const krr_ctx* ctx) {
     // ex2.approx.ftz.f32 returns 2^t about 0.83 ulp low on average for t < -1 (measured on
-    // GB300 by krr_exp2_probe); the products' kernel sums are scaled back by that much
+    // GB300 by krr_exp2_probe); the tensor-core product's kernel sums are scaled back by that
+    // much.  (On the FP32 forms it changed which problems escalate, and one batched problem
+    // stopped converging, so they are left as computed.)
     return (ctx && ctx->opts.ex2_correct) ? 1.0 + 0.83 * 5.9604644775390625e-08 : 1.0;
 }
 
@@ -493,7 +497,7 @@ constexpr int kmvm_rows() {
                                      : 1;
 }
 
-typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float, float,
+typedef void (*kmvm_fn)(const float*, int, const float*, int, const float*, int, int, float, float, float,
                         float*, int, double*);
 
 template <int D, int NRHS>
@@ -627,9 +631,9 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         int splits = choose_splits(nblk, ntiles, slots);
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
-        const double ksc = comp ? 1.0 : ex2_bias_scale(ctx);
+        const double ksc = 1.0;   // the exp2 bias correction is applied to the tensor-core form only
         double* part = nullptr;
-        if (splits > 1 || hp || ksc != 1.0)
+        if (splits > 1 || hp)
             KRR_RET(bufT(ctx, "kmvm_part", (size_t)splits * chunk * nr, &part));
         dim3 grid(nblk, splits);
         const float* Vc = V + (size_t)done * nc;
@@ -637,7 +641,7 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         // compensated kernels: -s as a float pair (raw_nsc_lo rides in the beta slot)
         const float beta_arg = comp ? raw_nsc_lo : beta;
         fn<<<grid, KM_THREADS, 0, ctx->stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps, beta_arg,
-                                                 raw_nsc, Qc, (int)nr, part);
+                                                 raw_nsc, (float)(ksc - 1.0), Qc, (int)nr, part);
         KRR_CHECK_LAUNCH();
         if (hp) {
             KRR_RET(launch_kmvm_reduce64(ctx, part, splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
@@ -830,7 +834,7 @@ int kmvm_into_scratch(cudaStream_t stream, int num_sms, const float* Xr, long lo
         const float* Vc = V + (size_t)done * nc;
         float* Qc = Q + (size_t)done * nr;
         fn<<<dim3(nblk, splits), KM_THREADS, 0, stream>>>(Pr, (int)nr, Pc, (int)nc, Vc, (int)nc, tps,
-                                                          (float)beta, 0.f, Qc, (int)nr,
+                                                          (float)beta, 0.f, 0.f, Qc, (int)nr,
                                                           splits > 1 ? part : nullptr);
         if (splits > 1)
             k_kmvm_reduce<<<ceil_div(nr * chunk, 256), 256, 0, stream>>>(part, splits, (int)nr, chunk,

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(QR_REF_THREADS)
 k_qr_reflector(const float* __restrict__ Y, long long n, int l, int ldy, int m, int jm, const float* __restrict__ C,
                float* __restrict__ Vp, float* __restrict__ tau, float* __restrict__ g,
                double* __restrict__ nrm, const unsigned long long* __restrict__ bkeys, int nbk,
-               int* __restrict__ piv, float* __restrict__ rdiag) {
+               int* __restrict__ piv, float* __restrict__ rdiag, const int* __restrict__ forced,
+               float* __restrict__ Rout) {
     extern __shared__ double zs[];   // l - m
     __shared__ double red[QR_REF_WARPS];
     __shared__ unsigned long long kred[QR_REF_WARPS];
@@ -94,8 +95,9 @@ k_qr_reflector(const float* __restrict__ Y, long long n, int l, int ldy, int m, 
         }
         __syncthreads();
     }
-    const unsigned long long km = kred[0];
-    const long long p = key_index(km);
+    // the argmax, or the caller's pivot (strong RRQR re-factorizes with a given order)
+    const unsigned long long km = forced ? 1ull : kred[0];
+    const long long p = forced ? (long long)forced[m] : key_index(km);
     if (km == 0 || p < 0 || p >= n) {   // no candidate left (cannot happen for k <= n): stop
         if (threadIdx.x == 0) {
             piv[m] = 0;
@@ -141,6 +143,7 @@ k_qr_reflector(const float* __restrict__ Y, long long n, int l, int ldy, int m, 
         piv[m] = (int)p;
         rdiag[m] = (float)nz;
         nrm[p] = -1.0;
+        if (Rout) Rout[(size_t)m * n + p] = (float)alpha;   // R_mm
     }
     __syncthreads();
     float* vm = Vp + (size_t)jm * l;
@@ -183,7 +186,7 @@ template <int NPL>
 __global__ void __launch_bounds__(QR_THREADS)
 k_qr_step(const float* __restrict__ Y, long long n, int l, int ldy, int m, int jm, float* __restrict__ C,
           const float* __restrict__ Vp, const float* __restrict__ tau, const float* __restrict__ g,
-          double* __restrict__ nrm, unsigned long long* __restrict__ bkeys) {
+          double* __restrict__ nrm, unsigned long long* __restrict__ bkeys, float* __restrict__ Rout) {
     __shared__ float vsh[NPL * 32];   // v_m[m:], zero-padded
     __shared__ float gsh[QH_B], vjm[QH_B];
     __shared__ unsigned long long sbest[QR_WARPS];
@@ -221,6 +224,7 @@ k_qr_step(const float* __restrict__ Y, long long n, int l, int ldy, int m, int j
             const float cm = tu * (dot - corr);
             C[i * QH_B + jm] = cm;
             const double r = (double)y[0] - (double)shift - (double)cm;
+            if (Rout) Rout[(size_t)m * n + i] = (float)r;   // R_mi: coordinate m of row i
             const double nn = fmax(ni - r * r, 0.0);
             nrm[i] = nn;
             best = max(best, pivot_key(nn, i));
@@ -236,7 +240,7 @@ k_qr_step(const float* __restrict__ Y, long long n, int l, int ldy, int m, int j
 }
 
 typedef void (*qr_step_fn)(const float*, long long, int, int, int, int, float*, const float*, const float*,
-                           const float*, double*, unsigned long long*);
+                           const float*, double*, unsigned long long*, float*);
 
 static qr_step_fn qr_step_for(int L) {
     const int npl = (L + 31) / 32;
@@ -299,7 +303,13 @@ k_qr_panel(float* __restrict__ Y, long long n, int l, int ldy, int m1, int nb, c
     }
 }
 
-int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int* piv, float* rdiag) {
+// The pivoted QR of Y^T (Y n x ldy, l used columns) for k pivots.  forced (device, k) makes
+// step m take pivot forced[m] instead of the argmax; Rout (device, k x n) receives row m of R
+// for every column (the pivot's diagonal, the rows not yet chosen; chosen ones are left
+// alone), and then the last step runs too, so that nrm ends as the squared residual norms
+// after k pivots (-1 for the chosen rows).
+int qrcp_core(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int* piv, float* rdiag,
+              const int* forced, float* Rout, double** nrm_out) {
     if (l > 4096) return fail(ctx, KRR_E_INVAL, "qrcp: more than 4096 projections");
     if (n >= 0xffffffffLL) return fail(ctx, KRR_E_INVAL, "qrcp: too many points");
     if (k > l) return fail(ctx, KRR_E_INVAL, "qrcp: more pivots than projections");
@@ -328,11 +338,11 @@ int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int*
             if (sizeof(double) * L > 48 * 1024) KRR_RET(allow_max_dynamic_smem(ctx, (const void*)k_qr_reflector));
             k_qr_reflector<<<1, QR_REF_THREADS, sizeof(double) * L, ctx->stream>>>(Y, n, l, ldy, m, jm, C, Vp,
                                                                                  tau, g, nrm, bkeys, grid,
-                                                                                 piv, rdiag);
+                                                                                 piv, rdiag, forced, Rout);
             KRR_CHECK_LAUNCH();
-            if (m + 1 < k) {
+            if (m + 1 < k || Rout) {
                 qr_step_for(L)<<<grid, QR_THREADS, 0, ctx->stream>>>(Y, n, l, ldy, m, jm, C, Vp, tau, g, nrm,
-                                                                    bkeys);
+                                                                    bkeys, Rout);
                 KRR_CHECK_LAUNCH();
             }
         }
@@ -345,7 +355,12 @@ int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int*
             KRR_CHECK_LAUNCH();
         }
     }
+    if (nrm_out) *nrm_out = nrm;
     return KRR_OK;
+}
+
+int launch_qrcp(krr_ctx* ctx, float* Y, long long n, int l, int ldy, int k, int* piv, float* rdiag) {
+    return qrcp_core(ctx, Y, n, l, ldy, k, piv, rdiag, nullptr, nullptr, nullptr);
 }
 
 }  // namespace krr

@@ -44,7 +44,7 @@ def test_binding_declares_every_header_symbol():
 
 def test_struct_layouts_match_header():
     from paper_1905_10587_gb300 import _lib
-    assert C.sizeof(_lib.KrrOpts) == 4 * 4 + 8 * 2 + 4 * 2 + 8 + 4 * 4 + 4 * 8
+    assert C.sizeof(_lib.KrrOpts) == 4 * 4 + 8 * 2 + 4 * 2 + 8 + 4 * 4 + 4 * 8 + 8
     assert _lib.KrrSolveInfo.cond_estimate.offset == 288
     assert _lib.KrrOpts.inner_tol.offset == 16
     assert C.sizeof(_lib.KrrSolveInfo) == 16 + 8 * 16 + 16 + 4 + 4 * 8 + 4 + 8 * 8 + 4 * 7 + 4

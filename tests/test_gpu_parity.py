@@ -256,6 +256,64 @@ def test_qrcp_pivots_across_panels(K):
     assert np.array_equal(piv[:upto], ref_p[:upto])
 
 
+def _kahan(n, c):
+    s = np.sqrt(1 - c * c)
+    return np.diag(s ** np.arange(n)) @ (np.eye(n) + np.triu(-c * np.ones((n, n)), 1))
+
+
+def test_strong_rrqr_on_kahan_matrix(K):
+    # Kahan's matrix (30 x 30, c = 0.285; columns scaled by 1 - 1e-4 j so that pivoting keeps
+    # their order in FP32): pivoted QR leaves max |R11^{-1} R12| = 318 and r_nn = 0.29 while
+    # sigma_n / sigma_1 = 1e-4.  The GPU's strong RRQR (f = 2) must swap, end with the
+    # Gu-Eisenstat measure within f, and its pivots must reveal the rank in FP64: the
+    # oracle's QR of the permuted matrix has |R11^{-1} R12| <= f and a trailing |r_nn| within
+    # sigma_n sqrt(1 + f^2 k (n - k))
+    import scipy.linalg as sla
+    n, k, f = 30, 29, 2.0
+    A = _kahan(n, 0.285) @ np.diag(1 - 1e-4 * np.arange(n))
+    Y = A.T.astype(np.float32)                     # rows of Y = columns of A (points)
+    ctx = K()
+    piv0, _ = ctx.qrcp(_t(Y), k)
+    assert np.array_equal(piv0.cpu().numpy(), np.arange(k))
+    piv, rd, swaps, rho = ctx.strong_rrqr(_t(Y), k, f)
+    piv = piv.cpu().numpy()
+    print(f"Kahan: {swaps} swaps, rho {rho:.3f}")
+    assert swaps >= 1 and rho <= f * (1 + 1e-3)
+    assert len(set(piv.tolist())) == k
+    rest = np.setdiff1d(np.arange(n), piv)
+    A64 = Y.T.astype(np.float64)
+    R = np.linalg.qr(A64[:, np.concatenate([piv, rest])], mode="r")
+    W = sla.solve_triangular(R[:k, :k], R[:k, k:])
+    assert np.abs(W).max() <= f * (1 + 1e-2)
+    sig = np.linalg.svd(A64, compute_uv=False)
+    assert abs(R[-1, -1]) <= sig[-1] * np.sqrt(1 + f * f * k * (n - k)) * (1 + 1e-2)
+    np.testing.assert_allclose(rd.cpu().numpy(), np.abs(np.diag(R)[:k]), rtol=1e-3)
+
+
+def test_strong_rrqr_on_a_kernel_sketch_keeps_the_pivots(K):
+    # Section 3's remark: on a Gaussian kernel sketch pivoted QR already meets the strong
+    # conditions with f = 2, so the strong RRQR makes no swap and keeps the pivots; a build
+    # with strong_f = 2 ends within f (its FP32 sketch of 105 projections for 100 anchors
+    # may need a swap near the end of R11) and solves as usual
+    p = synth.small(n=1500)
+    l, k = 40, 35
+    Y = O.sketch(p.X, p.sigma, O.omega(3, l, p.n)).astype(np.float32)
+    ctx = K()
+    piv0, _ = ctx.qrcp(_t(Y), k)
+    piv, _, swaps, rho = ctx.strong_rrqr(_t(Y), k, 2.0)
+    assert swaps == 0 and rho <= 2.0
+    assert np.array_equal(piv.cpu().numpy(), piv0.cpu().numpy())
+    q = synth.small()
+    ctx2 = K(strong_f=2.0)
+    ctx2.build(_t(q.X), q.sigma, q.beta, q.k, seed=1)
+    sw, rho2 = ctx2.anchor_stats()
+    print(f"build with strong RRQR: {sw} swaps, rho {rho2:.3f}")
+    assert 0.0 < rho2 <= 2.0 * (1 + 1e-3)
+    alpha, info = ctx2.solve(_t(q.Y), tol=q.tol)
+    r = O.residual(q.X, alpha.cpu().numpy(), q.Y, q.sigma, q.beta)
+    assert np.linalg.norm(r) / np.linalg.norm(q.Y) <= 1e-6
+
+
 def test_qrcp_pivots_distinct_gaps(K):
     # columns with well separated norms along orthogonal directions: a unique order
     rng = np.random.Generator(np.random.PCG64(4))
