@@ -460,10 +460,14 @@ def _alu_bound(sms: int, sm_hz: float, fma_ops: float) -> float:
     return min(sms * 128 * sm_hz / max(fma_ops, 1e-9), sms * 32 * sm_hz)
 
 
-def _form_fma_ops(form: int, d: int, nrhs: int) -> float:
-    """FMA-pipe operations per pair: tensor-core form r FFMA; FP32 expansion d + 1 + r;
-    exact differences 2 d + 2 + r (r right-hand sides)."""
-    return nrhs if form == 1 else (d + 1 + nrhs if form == 0 else 2 * d + 2 + nrhs)
+def _form_fma_ops(form: int, d: int, nrhs: int, tc_pv: bool = True) -> float:
+    """FMA-pipe operations per pair: tensor-core form r FFMA, or with blocks of 8 or 16
+    right-hand sides contracted on the tensor cores 2 (the 2^15 scale and the FP16 split's
+    mixed FMA), so the ex2 bounds it; FP32 expansion d + 1 + r; exact differences
+    2 d + 2 + r (r right-hand sides)."""
+    if form == 1:
+        return 2 if (tc_pv and nrhs >= 8) else nrhs
+    return d + 1 + nrhs if form == 0 else 2 * d + 2 + nrhs
 
 
 def batched_extra(api, sms: int, sm_hz: float, workers: int = 8) -> dict:
@@ -513,9 +517,9 @@ def cube_extra(api, sms: int, sm_hz: float, reps: int = 3) -> dict:
     X = torch.from_numpy(p.X).cuda()
     Y = torch.from_numpy(p.Y).cuda()
     out = {"workload": f"cube n={p.n} d={p.d} sigma={p.sigma:g} beta={p.beta:g}"}
-    for prec in (1, 2):
-        ctx = api.KRR(precision=prec)
-        for nrhs in (1, 16):
+    for prec, tc_pv in ((1, 1), (2, 1), (1, 0)):
+        ctx = api.KRR(precision=prec, tc_pv=tc_pv)
+        for nrhs in ((1, 16) if tc_pv else (16,)):
             V = Y[:, :nrhs].contiguous()
             ctx.kmvm(X, X, V, p.sigma, p.beta)
             torch.cuda.synchronize()
@@ -527,9 +531,9 @@ def cube_extra(api, sms: int, sm_hz: float, reps: int = 3) -> dict:
             e1.synchronize()
             ms = e0.elapsed_time(e1) / reps
             rate = float(p.n) ** 2 / (ms / 1e3)
-            bound = _alu_bound(sms, sm_hz, _form_fma_ops(prec, p.d, nrhs))
-            out[f"prec{prec}_nrhs{nrhs}"] = {"ms": ms, "pairs_per_s": rate, "frac": rate / bound,
-                                             "bound_pairs_per_s": bound}
+            bound = _alu_bound(sms, sm_hz, _form_fma_ops(prec, p.d, nrhs, bool(tc_pv)))
+            key = f"prec{prec}_nrhs{nrhs}" + ("" if tc_pv else "_pv_fma")
+            out[key] = {"ms": ms, "pairs_per_s": rate, "frac": rate / bound, "bound_pairs_per_s": bound}
         ctx.close()
     return out
 
@@ -686,14 +690,16 @@ def run_condition(args):
         for k in (0, 100, 500, 1000):
             # no reliable-update replacement before convergence: the Lanczos estimate uses
             # the whole uninterrupted recurrence
+            # anchor_rtol = 0: exactly k anchors unless a Cholesky pivot gives out (k_eff)
             ctx = api.KRR(precision=1, no_precond=1 if k == 0 else 0, max_iter=20000 if k else 3000,
-                          refine_max=200, inner_tol=1e-12)
+                          refine_max=200, inner_tol=1e-12, anchor_rtol=0.0)
             ctx.build(X, p.sigma, p.beta, max(k, 1), seed=1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, info = ctx.solve(Y, tol=1e-6, allow_noconv=True)
             torch.cuda.synchronize()
-            rows.append({"set": name, "n": p.n, "k": k, "cond_estimate": info["cond_estimate"],
+            rows.append({"set": name, "n": p.n, "k": k, "k_eff": info.get("k_eff", 0) if k else 0,
+                         "cond_estimate": info["cond_estimate"],
                          "lanczos_steps": info["lanczos_steps"], "iters": info["iters"],
                          "rel_residual": info["rel_residual"][0], "seconds": time.perf_counter() - t0})
             print(json.dumps(rows[-1]), flush=True)

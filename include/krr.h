@@ -103,7 +103,12 @@ typedef struct krr_opts {
                              (precision 1) by 1 + 0.83 * 2^-24, the mean low bias of the
                              hardware 2^t approximation for t < -1 (see krr_exp2_probe);
                              0: uncorrected                                              */
-    int    reserved[4];
+    int    tc_pv;         /* 1 (default): in the tensor-core product, blocks of 8 or 16
+                             right-hand sides contract P V on the tensor cores too (P and
+                             V as FP16 hi + lo pairs, about 2^-22 relative per entry;
+                             FP32 V and Q only); 2: every block, 1 to 16 right-hand
+                             sides; 0: P V as FP32 FMAs                                 */
+    int    reserved[3];
     double strong_f;      /* 0 (default): the build selects anchors by pivoted QR (Algorithm 1
                              step 3 as Section 3 remarks); f > 1: by strong RRQR with bound
                              f (Gu-Eisenstat; the factorization Eq. (4) assumes), see
@@ -171,7 +176,10 @@ int krr_profile_read(krr_ctx* ctx, const char* phase, double* total_ms, long lon
  * the host.  variant 0: one K = 16 step in the unswizzled core-matrix layout (the
  * sketch's P and Omega operands); variant 1 swaps its two strides (must fail);
  * variant 2: K = 64 in four steps in the 128-byte swizzled layout of the point
- * features; variant 3 reads that data through an unswizzled descriptor (must fail).
+ * features; variant 3 reads that data through an unswizzled descriptor (must fail);
+ * variant 4: FP16 with K = 64, A held in tensor memory (two K-neighbours per 32-bit
+ * column, the even one in the low half) and B in the swizzled layout, the form of
+ * the multi-RHS product's P.V step.
  * Writes the number of wrong entries and the largest error (host outputs).  No
  * counterpart in the paper: a check of the hardware encoding the tensor-core
  * product relies on. */
@@ -384,6 +392,25 @@ typedef struct krr_problem {
 
 int krr_batch_solve(const krr_problem* probs, int nprob, int nrhs, double tol, unsigned long long seed,
                     const krr_opts* opts, int workers, krr_solve_info* infos, int* statuses);
+
+/* The same contract, solved in lockstep: after the builds (W threads as above), the PCG
+ * recurrences of all problems advance together on one stream, and each step of an
+ * iteration is one launch over the work items of every active problem (the tensor-core
+ * product with P.V on the tensor cores for problems built with precision 1 and d <= 16,
+ * the CG vector updates, the Woodbury apply, the per-problem CG scalars).  Each problem
+ * keeps its own scalars, column activity and true-residual replacements; the host reads
+ * all problems' recursive residuals once per iteration.  A problem whose recurrence
+ * breaks down, stalls, shows repeated residual gaps or runs out of iterations is then
+ * solved again from zero by krr_solve on its own context (which escalates the product
+ * form), so every problem ends as the one-by-one path would end it; its info counts the
+ * grouped iterations too.  solve_ms is the wall time of the grouped phase (shared).
+ * Device memory: the five concatenated FP32 vectors (sum of n x nrhs each) plus per
+ * problem the Woodbury partials and the product's split partials.  Problems need
+ * n <= 2^30.  Returns as krr_batch_solve; KRR_E_TIMEOUT when a bounded wait of the
+ * grouped product ran out (every problem is then finished by its own solve). */
+int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int nrhs, double tol,
+                            unsigned long long seed, const krr_opts* opts, int workers,
+                            krr_solve_info* infos, int* statuses);
 
 #ifdef __cplusplus
 }

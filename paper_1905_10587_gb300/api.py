@@ -309,8 +309,10 @@ def peak_probe(kind: int) -> float:
     return v.value
 
 
-def batch_solve(problems, tol: float = 1e-6, seed: int = 0, workers: int = 8, **opts):
-    """Solve independent problems concurrently (krr_batch_solve).
+def batch_solve(problems, tol: float = 1e-6, seed: int = 0, workers: int = 8, grouped: bool = False,
+                **opts):
+    """Solve independent problems concurrently (krr_batch_solve), or in lockstep with one
+    launch per step over all problems (krr_batch_solve_grouped, grouped=True).
 
     problems: list of (X (n, d), Y (n, nrhs) or (n,), sigma, beta, k) CUDA tensors/values,
     all with the same number of right-hand sides.  Returns (list of FP64 alpha tensors,
@@ -337,13 +339,15 @@ def batch_solve(problems, tol: float = 1e-6, seed: int = 0, workers: int = 8, **
     infos = (L.KrrSolveInfo * len(problems))()
     stats = (C.c_int * len(problems))()
     torch.cuda.synchronize()
-    rc = lib.krr_batch_solve(arr, len(problems), nrhs, tol, seed, C.byref(o), workers, infos, stats)
+    fn = lib.krr_batch_solve_grouped if grouped else lib.krr_batch_solve
+    rc = fn(arr, len(problems), nrhs, tol, seed, C.byref(o), workers, infos, stats)
     if rc not in (0, L.KRR_E_NOCONV):
         raise KRRError(rc, "batch solve failed")
     out = [_uncols(A, vec) for A, vec in alphas]
     info = [dict(status=f.status, iters=f.iters, sweeps=f.sweeps, k_eff=f.k_eff,
                  rel_residual=[f.rel_residual[j] for j in range(nrhs)], solve_ms=f.solve_ms,
-                 build_ms=f.build_ms, mvm_count=f.mvm_count, product_form=f.product_form)
+                 build_ms=f.build_ms, mvm_count=f.mvm_count, product_form=f.product_form,
+                 restarts=f.restarts)
             for f in infos]
     return out, info, list(stats)
 

@@ -98,9 +98,6 @@ int launch_cg_alpha(krr_ctx* ctx, const float* p, const float* q, int nrhs, doub
 int launch_cg_update_xr(krr_ctx* ctx, float* x, float* r, const float* p, const float* q, int nrhs,
                         double* part, double tol2);
 int launch_cg_beta_p(krr_ctx* ctx, float* p, const float* z, int nrhs, const double* rz_part);
-int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot);
-int launch_convert_up(krr_ctx* ctx, const float* a, double* b, long long tot);
-int launch_accumulate(krr_ctx* ctx, const float* x, double* y, long long tot);
 int launch_cg_set_active(krr_ctx* ctx, const int* act_host, int nrhs);
 int launch_identity_apply(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part);
 int launch_identity_apply64(krr_ctx* ctx, const double* R, int nrhs, double* Z, double* rz_part);
@@ -291,7 +288,7 @@ static int ensure_raw_points(krr_ctx* ctx) {
 
 // (K + beta I) V for the built point set in product form 0 (FP32 expansion), 1 (tensor
 // cores, when built) or 2 (FP32 on raw coordinate differences).
-static int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q, int form) {
+int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q, int form) {
     if (form == 1 && ctx->FA)
         return launch_kmvm_tc(ctx, ctx->FA, ctx->n, ctx->FB, ctx->n, ctx->d, (float)ctx->beta, V, nrhs, Q);
     if (form == 2) {
@@ -349,6 +346,7 @@ int krr_default_opts(krr_opts* o) {
     o->escalate = 1;
     o->recurrence = 0;
     o->ex2_correct = 1;
+    o->tc_pv = 1;
     return KRR_OK;
 }
 
@@ -368,7 +366,8 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.test_stall_copies < 0 || ctx->opts.test_stall_copies > 1 ||
         ctx->opts.recurrence < 0 || ctx->opts.recurrence > 2 ||
         ctx->opts.no_precond < 0 || ctx->opts.no_precond > 1 ||
-        ctx->opts.ex2_correct < 0 || ctx->opts.ex2_correct > 1 ||
+        ctx->opts.ex2_correct < 0 || ctx->opts.ex2_correct > 1 || ctx->opts.tc_pv < 0 ||
+        ctx->opts.tc_pv > 2 ||
         !(ctx->opts.strong_f == 0.0 || ctx->opts.strong_f > 1.0) || ctx->opts.strong_swaps < 0 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;
@@ -723,9 +722,6 @@ int krr_precond_apply(krr_ctx* ctx, const float* In, int nrhs, float* Out) {
     return launch_apply_precond(ctx, In, nrhs, Out, nullptr);
 }
 
-// A replacement whose true residual norm exceeds twice the recursive one restarts the
-// recurrence (squared norms compared).
-static constexpr double kGapRestart2 = 4.0;
 
 // (K + beta I) p for FP64 p (n x nrhs): p split into FP32 hi/lo column pairs, FP64 sums out.
 static int square_product64(krr_ctx* ctx, const double* p64, int nrhs, float* psplit, double* q64,

@@ -187,6 +187,12 @@ __device__ __forceinline__ float ex2_reduced(float t) {
     return t < -125.f ? 0.f : r;
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -231,6 +237,37 @@ int launch_kmvm_reduce(krr_ctx* ctx, const double* part, int splits, int nr, int
 // Q = (dK/dlog sigma)(Pr, Pc) v, one column
 int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc,
                        int d, const float* V, float* Q);
+
+// One problem of a (possibly grouped) tensor-core product with P.V on the tensor cores:
+// its features, V tiles, per-column scales, partial sums and work split.  Its items are
+// item0 .. item0 + items - 1 of the launch, item li = (row block li / splits, column
+// split li % splits); tps column tiles per split.
+struct PvProb {
+    const unsigned char* FA;
+    const unsigned char* FB;
+    const unsigned char* Vt;
+    const double* vsc;
+    double* part;
+    int nr, nc, Kp, splits, tps, items, item0, pad;
+};
+// One problem of the grouped V preparation: V (n entries per column, ldv apart) into the
+// tiles Vt (ncp columns), scale exponents vexp and factors vsc; its blocks start at blk0.
+struct PvPrep {
+    const float* V;
+    unsigned char* Vt;
+    int* vexp;
+    double* vsc;
+    int ldv, n, ncp, blk0;
+};
+int pv_tile_bytes(int nrhs);
+int launch_pv_prep_grouped(krr_ctx* ctx, const PvPrep* tab_dev, int nprob, int nblk, int nrhs);
+int launch_kmvm_tcpv_table(krr_ctx* ctx, const PvProb* table_dev, int nprob, int items, int nrhs,
+                           int kp_max, int* err);
+// (K + beta I) V for the built point set in product form 0, 1 or 2 (api.cu)
+int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q, int form);
+// A replacement whose true residual norm exceeds twice the recursive one restarts the
+// recurrence (squared norms compared).
+constexpr double kGapRestart2 = 4.0;
 
 // tc_kmvm.cu: BF16x3 tcgen05 product (d <= 16).  Features: role 0 rows, 1 columns.
 int tc_feature_kp(int d);
@@ -284,6 +321,10 @@ int launch_add_diag(krr_ctx* ctx, double* A, int k, double v);
 
 // cg.cu
 int launch_apply_precond(krr_ctx* ctx, const float* R, int nrhs, float* Z, double* rz_part_out);
+// b = (float) a; b = (double) a; y += x (tot elements)
+int launch_convert(krr_ctx* ctx, const double* a, float* b, long long tot);
+int launch_convert_up(krr_ctx* ctx, const float* a, double* b, long long tot);
+int launch_accumulate(krr_ctx* ctx, const float* x, double* y, long long tot);
 // cg64.cu: FP64 recurrence (split product input, FP64 apply and CG updates)
 int launch_split_hilo(krr_ctx* ctx, const double* a, long long n, int nrhs, float* out);
 int launch_apply_precond64(krr_ctx* ctx, const double* R, int nrhs, double* Z, double* rz_part);

@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace krr {
 
@@ -124,6 +125,56 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// 32 lanes x 32 consecutive 32-bit columns from registers (thread = lane), then wait
+// until the stores are done.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns into registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+// D[tmem] (+)= A[tmem] * B[smem]^T, FP16 inputs, FP32 accumulation.  A (M = 128) sits in
+// TMEM lane = row, two K-neighbours per 32-bit column (the even one in the low half).
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Two floats as one f16x2 word, round to nearest: lo in bits 0-15, hi in bits 16-31.
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // Shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x
 // 16 bytes stored as contiguous 128-byte blocks; lbo = byte distance between core
 // matrices adjacent along K, sbo = between 8-row groups; bits 46-47 = 1 (version),
@@ -156,6 +207,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// The same with A and B FP16 (type code 0).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // Byte offset of element (r, k) in the core-matrix tiled layout of a tile with Kp columns.
 __host__ __device__ inline uint32_t tile_off(int r, int k, int Kp) {
@@ -174,7 +229,9 @@ __host__ __device__ inline uint32_t tile_off_sw(int r, int k, int rows) {
 // variant 0: one K=16 step in the core-matrix layout, lbo = 128 (K neighbours), sbo = 256
 // (row groups); variant 1 swaps them; variant 2: K = 64 in four steps in the 128-byte
 // swizzled layout (the feature layout); variant 3 reads that swizzled data through an
-// unswizzled descriptor.  Every address stays inside the 20 KB of operands.
+// unswizzled descriptor; variant 4: FP16, K = 64 in four steps with A stored in TMEM
+// (columns 32..63) and B in the swizzled layout (the multi-RHS product's P.V step).
+// Every address stays inside the 20 KB of operands and the 64 TMEM columns.
 __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restrict__ out,
                                                      int* __restrict__ err) {
     __shared__ __align__(1024) unsigned char sA[128 * 64 * 2];
@@ -184,7 +241,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restr
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool sw = variant >= 2;
     const int K = sw ? 64 : 16;
-    for (int e = tid; e < 128 * K; e += 128) {
+    for (int e = tid; e < 128 * K && variant != 4; e += 128) {
         const int r = e / K, k = e % K;
         const float v = (float)((r % 7) - 3 + (k % 3));
         *reinterpret_cast<__nv_bfloat16*>(sA + (sw ? tile_off_sw(r, k, 128) : tile_off(r, k, 16))) =
@@ -193,8 +250,11 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restr
     for (int e = tid; e < 32 * K; e += 128) {
         const int c = e / K, k = e % K;
         const float v = (float)((c % 5) - 2 + (k % 4));
-        *reinterpret_cast<__nv_bfloat16*>(sB + (sw ? tile_off_sw(c, k, 32) : tile_off(c, k, 16))) =
-            __float2bfloat16_rn(v);
+        if (variant == 4)
+            *reinterpret_cast<__half*>(sB + tile_off_sw(c, k, 32)) = __float2half_rn(v);
+        else
+            *reinterpret_cast<__nv_bfloat16*>(sB + (sw ? tile_off_sw(c, k, 32) : tile_off(c, k, 16))) =
+                __float2bfloat16_rn(v);
     }
     if (tid == 0) {
         mbar_init(&bar, 1);
@@ -202,14 +262,29 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restr
     }
     fence_proxy_async();
     __syncthreads();
-    if (warp == 0) tmem_alloc(&tbase, 32);
+    if (warp == 0) tmem_alloc(&tbase, 64);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tbase;
+    if (variant == 4) {   // A (row = warp * 32 + lane) into TMEM columns 32..63
+        const int r = warp * 32 + lane;
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            pk[c] = pack_f16x2((float)((r % 7) - 3 + ((2 * c) % 3)), (float)((r % 7) - 3 + ((2 * c + 1) % 3)));
+        tmem_st32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, pk);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
     const uint32_t lbo = variant == 0 ? 128u : 256u, sbo = variant == 0 ? 256u : 128u;
     if (tid == 0) {
-        if (variant == 2) {          // four K steps of 16 inside the swizzle atom
+        if (variant == 4) {          // A from TMEM: 8 columns (16 FP16) per K step
+            for (int kk = 0; kk < 4; ++kk)
+                mma_f16_ts(tmem, tmem + 32u + 8u * kk, smem_desc_sw128(smem_u32(sB) + 32u * kk),
+                           idesc_f16(128, 32), kk > 0 ? 1u : 0u);
+        } else if (variant == 2) {   // four K steps of 16 inside the swizzle atom
             for (int kk = 0; kk < 4; ++kk)
                 mma_bf16(tmem, smem_desc_sw128(smem_u32(sA) + 32u * kk),
                          smem_desc_sw128(smem_u32(sB) + 32u * kk), idesc_bf16(128, 32), kk > 0 ? 1u : 0u);
@@ -236,7 +311,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(int variant, float* __restr
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 32);
+    if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
 // ------------------------------------------------------------------ features
@@ -292,21 +367,26 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
 // ------------------------------------------------------------------ product kernel
 // Warp-specialised persistent CTA (one per SM): warp 0 lane 0 streams feature tiles
 // with cp.async.bulk, warp 1 lane 0 issues tcgen05.mma, warps 2..17 are the epilogue.
+// A work item is 128 rows (one M = 128 MMA) against a range of 256-column tiles.  Every
+// tcgen05.mma of this kind takes about 194 cycles whatever its N (measured on GB300 for
+// N = 16 .. 256, A in shared or tensor memory, one or several accumulators), so the
+// exponent MMAs run at the widest N, 256: Kp / 16 MMAs per 32768 pairs, which at Kp = 64
+// (d <= 9) is 776 cycles against 1024 cycles of ex2 at 32 per clock.
 // Hand-offs are mbarrier full/empty pairs only (no block-wide barrier in the loop):
-//   a_full / a_empty          the 256-row operand of the current work item
+//   a_full / a_empty          the 128-row operand of the current work item
 //   s_full[s] / s_empty[s]    column tile stage s (empty needs the MMA commit and the
 //                             8 epilogue warps of the tile's parity, which read V from it)
 //   t_full[b] / t_empty[b]    TMEM accumulator buffer b (2 x 256 columns), read by the
 //                             8 epilogue warps of parity b
 constexpr int TC_EPI_WARPS = 16;
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
-constexpr int TC_BN = 128;        // columns per tile
-constexpr int TC_ROWS = 256;      // rows per work item
-constexpr int TC_NS = 4;          // pipeline stages for column tiles
-static_assert(TC_NS % 2 == 0, "a stage must always hold tiles of one parity");
+constexpr int TC_BN = 256;        // columns per tile
+constexpr int TC_ROWS = 128;      // rows per work item
+constexpr int TC_NSMAX = 4;       // most pipeline stages; the count is even, so that a
+                                  // stage always holds tiles of one parity
 
 struct TcShared {
-    uint64_t a_full, a_empty, s_full[TC_NS], s_empty[TC_NS], t_full[2], t_empty[2], drain;
+    uint64_t a_full, a_empty, s_full[TC_NSMAX], s_empty[TC_NSMAX], t_full[2], t_empty[2], drain;
     uint32_t tbase;
     int abort;
 };
@@ -319,22 +399,23 @@ template <int NRHS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
           int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
-          int tiles_per_split, double* __restrict__ part, int* __restrict__ err,
+          int tiles_per_split, int ns, double* __restrict__ part, int* __restrict__ err,
           long long wlimit, int stall_copies) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzle atoms need 1024-byte alignment; the launch adds 1 KB of slack for this
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t tileA = 128u * Kp * 2u;            // bytes of one 128-row feature tile
-    unsigned char* sA = smem;                         // 2 tiles (256 rows)
-    unsigned char* sB = smem + 2 * tileA;             // TC_NS column tiles
-    float* sV = reinterpret_cast<float*>(sB + TC_NS * tileA);   // TC_NS x NRHS x TC_BN
-    TcShared* sh = reinterpret_cast<TcShared*>(sV + TC_NS * NRHS * TC_BN);
+    const uint32_t tileB = 2u * tileA;                // a 256-column tile: slab-major, 256 rows
+    unsigned char* sA = smem;                         // the item's 128 rows
+    unsigned char* sB = smem + tileA;                 // ns column tiles
+    float* sV = reinterpret_cast<float*>(sB + (size_t)ns * tileB);   // ns x NRHS x TC_BN
+    TcShared* sh = reinterpret_cast<TcShared*>(sV + ns * NRHS * TC_BN);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         mbar_init(&sh->a_full, 1);
         mbar_init(&sh->a_empty, 1);
-        for (int s = 0; s < TC_NS; ++s) {
+        for (int s = 0; s < TC_NSMAX; ++s) {
             mbar_init(&sh->s_full[s], 1);
             mbar_init(&sh->s_empty[s], 1 + TC_EPI_WARPS / 2);   // MMA + the 8 warps of its parity
         }
@@ -354,6 +435,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     const uint32_t tmem = sh->tbase;
     const int ntiles = (nc + TC_BN - 1) / TC_BN;
     const uint32_t vbytes = NRHS * TC_BN * 4u;
+    const int nslab = Kp / 64;
     volatile int* abort = &sh->abort;
     auto give_up = [&]() {
         *abort = 1;
@@ -371,15 +453,22 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 const int t0 = sp * tiles_per_split;
                 const int t1 = min(t0 + tiles_per_split, ntiles);
                 if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u, wlimit)) { give_up(); break; }
-                mbar_expect_tx(&sh->a_full, 2 * tileA);
-                bulk_g2s(sA, FA + (size_t)rb * 2 * tileA, 2 * tileA, &sh->a_full);
+                mbar_expect_tx(&sh->a_full, tileA);
+                bulk_g2s(sA, FA + (size_t)rb * tileA, tileA, &sh->a_full);
                 ++ic;
                 bool ok = true;
                 for (int t = t0; t < t1; ++t) {
-                    const int s = g % TC_NS;
-                    if (!mbar_wait(&sh->s_empty[s], ((g / TC_NS) & 1u) ^ 1u, wlimit)) { ok = false; break; }
-                    mbar_expect_tx(&sh->s_full[s], tileA + vbytes);
-                    bulk_g2s(sB + s * tileA, FB + (size_t)t * tileA, tileA, &sh->s_full[s]);
+                    const int s = (int)(g % (uint32_t)ns);
+                    if (!mbar_wait(&sh->s_empty[s], ((g / ns) & 1u) ^ 1u, wlimit)) { ok = false; break; }
+                    mbar_expect_tx(&sh->s_full[s], tileB + vbytes);
+                    // feature tiles 2t and 2t + 1 (128 rows each, slab-major) become one
+                    // 256-row tile per 64-wide K slab: slab sl at sl x 32 KB, rows 128.. at +16 KB
+                    unsigned char* dB = sB + (size_t)s * tileB;
+                    for (int sl = 0; sl < nslab; ++sl)
+                        for (int hf = 0; hf < 2; ++hf)
+                            bulk_g2s(dB + sl * 32768u + hf * 16384u,
+                                     FB + (size_t)(2 * t + hf) * tileA + (size_t)sl * 16384u, 16384u,
+                                     &sh->s_full[s]);
                     float* dV = sV + s * NRHS * TC_BN;
                     for (int q = 0; q < NRHS; ++q)
                         bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u,
@@ -391,9 +480,9 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             // Drain: every copy issued lands before the CTA may exit.  Each barrier has
             // one arrival per phase (this thread's expect_tx), so the phase of the last
             // copy into it is the newest one and a parity wait on it is exact.
-            for (uint32_t i = 0; i < (g < (uint32_t)TC_NS ? g : (uint32_t)TC_NS); ++i) {
+            for (uint32_t i = 0; i < (g < (uint32_t)ns ? g : (uint32_t)ns); ++i) {
                 const uint32_t gg = g - 1 - i;
-                mbar_wait(&sh->s_full[gg % TC_NS], (gg / TC_NS) & 1u, wlimit);
+                mbar_wait(&sh->s_full[gg % ns], (gg / ns) & 1u, wlimit);
             }
             if (ic > 0) mbar_wait(&sh->a_full, (ic - 1) & 1u, wlimit);
         }
@@ -411,21 +500,20 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 if (!mbar_wait(&sh->a_full, ic & 1u, wlimit)) { give_up(); break; }
                 bool ok = true;
                 for (int t = t0; t < t1; ++t, ++g) {
-                    const int s = g % TC_NS, b = g & 1;
-                    if (!mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u, wlimit)) { ok = false; break; }
+                    const int s = (int)(g % (uint32_t)ns), b = g & 1;
+                    if (!mbar_wait(&sh->s_full[s], (g / ns) & 1u, wlimit)) { ok = false; break; }
                     if (!mbar_wait(&sh->t_empty[b], ((g >> 1) & 1u) ^ 1u, wlimit)) { ok = false; break; }
                     issued = true;
                     tc_fence_after();
-                    const uint32_t b_addr = smem_u32(sB + s * tileA);
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t d = tmem + (uint32_t)(b * 256 + h * 128);
-                        for (int kk = 0; kk < Kp / 16; ++kk) {
-                            // slab kk / 4 (128 rows x 128 bytes), 32 bytes per K step inside it
-                            const uint32_t koff = (uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u;
-                            const uint64_t ad = smem_desc_sw128(a_addr + h * tileA + koff);
-                            const uint64_t bd = smem_desc_sw128(b_addr + koff);
-                            mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
-                        }
+                    const uint32_t b_addr = smem_u32(sB + (size_t)s * tileB);
+                    const uint32_t d = tmem + (uint32_t)(b * TC_BN);
+                    for (int kk = 0; kk < Kp / 16; ++kk) {
+                        // 32 bytes per K step inside a slab; slabs 16 KB apart for the 128
+                        // rows of A, 32 KB apart for the 256 rows of B
+                        const uint32_t kin = (uint32_t)(kk & 3) * 32u;
+                        const uint64_t ad = smem_desc_sw128(a_addr + (uint32_t)(kk >> 2) * 16384u + kin);
+                        const uint64_t bd = smem_desc_sw128(b_addr + (uint32_t)(kk >> 2) * 32768u + kin);
+                        mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
                     mma_commit(&sh->t_full[b]);
                     mma_commit(&sh->s_empty[s]);
@@ -442,14 +530,15 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        // Warp e (0..15) reads TMEM lanes of its quarter (warp & 3), rows of its half of
-        // the 256-row item, all 128 columns, for the tiles of its parity only: on each
-        // SM sub-partition two warps work on even tiles and two on odd ones, so the TMEM
-        // load latency of one pair hides behind the exponentials of the other.
+        // Warp e (0..15) reads TMEM lanes of its quarter (warp & 3), i.e. 32 rows of the
+        // 128-row item, and 128 of the 256 columns (its column half), for the tiles of
+        // its parity only: on each SM sub-partition two warps work on even tiles and two
+        // on odd ones, so the TMEM load latency of one pair hides behind the exponentials
+        // of the other.
         const int e = warp - 2;                       // 0..15
         const int quarter = warp & 3;                 // TMEM lanes this warp may read
-        const int half = (e >> 2) & 1, par = e >> 3;
-        const int lrow = half * 128 + quarter * 32 + lane;
+        const int chalf = (e >> 2) & 1, par = e >> 3;
+        const int lrow = quarter * 32 + lane;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
             const int rb = item / splits, sp = item - rb * splits;
@@ -467,14 +556,14 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             bool ok = true;
             for (int t = t0; t < t1; ++t, ++g) {
                 if ((int)(g & 1u) != par) continue;
-                const int s = g % TC_NS, b = par;
+                const int s = (int)(g % (uint32_t)ns), b = par;
                 ok = mbar_wait(&sh->t_full[b], (g >> 1) & 1u, wlimit) &&
-                     mbar_wait(&sh->s_full[s], (g / TC_NS) & 1u, wlimit);
+                     mbar_wait(&sh->s_full[s], (g / ns) & 1u, wlimit);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) { if (lane == 0) give_up(); break; }
                 tc_fence_after();
-                const float* v = sV + s * NRHS * TC_BN;
-                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + half * 128);
+                const float* v = sV + s * NRHS * TC_BN + chalf * 128;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TC_BN + chalf * 128);
                 // one 32-column chunk of exponents r (columns 32 hh .. 32 hh + 31)
                 auto chunk = [&](const uint32_t (&r)[32], int hh) {
 #pragma unroll
@@ -498,7 +587,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
                 };
-                static_assert(TC_BN == 128, "four 32-column chunks per tile");
+                static_assert(TC_BN == 256, "four 32-column chunks per column half");
                 if constexpr (NRHS <= 2) {
                     // two register sets: the load of chunk c + 1 is in flight while chunk c
                     // is exponentiated
@@ -519,11 +608,11 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 } else {
                     // 32 live registers for the exponents
 #pragma unroll 1
-                    for (int hh = 0; hh < TC_BN / 32; ++hh) {
+                    for (int hh = 0; hh < 4; ++hh) {
                         uint32_t r0[32];
                         tmem_ld32(tb + 32 * hh, r0);
                         tmem_wait_ld(r0);
-                        if (hh == TC_BN / 32 - 1) release();
+                        if (hh == 3) release();
                         chunk(r0, hh);
                     }
                 }
@@ -544,7 +633,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             if (row < nr) {
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q)
-                    part[(((size_t)sp * 2 + par) * NRHS + q) * nr + row] = acc64[q];
+                    part[(((size_t)sp * 4 + par * 2 + chalf) * NRHS + q) * nr + row] = acc64[q];
             }
         }
     }
@@ -554,6 +643,414 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------------ multi-RHS product
+// With R right-hand sides the contraction sum_j P_ij V_jq (P_ij = 2^t_ij) is a GEMM
+// of its own and runs as a second tcgen05 MMA chained to the exponent MMA, P held in TMEM:
+//   EXP   S (128 x 64) = FA(128 rows) . FB(64 columns)^T   (the BF16 x3 split above)
+//   split P' = 2^15 2^S = Ph + Pl, both FP16 (22 significant bits), written over S in
+//         place: of every 32 TMEM columns, 16 hold Ph and 16 hold Pl (two K per column)
+//   PV    C (128 x 2R) += Ph . [Vh; Vl]^T + Pl . [Vh; (Vl)]^T  (Pl . Vl unless R = 16)
+// with V'_q = 2^e_q V_q (e_q puts max |V'_q| in [2^14, 2^15)) split V' = Vh + Vl in FP16.
+// Every product of two FP16 values is exact in FP32; the representation errors are
+// about 2^-22 relative per entry (the dropped Pl . Vl term when R = 16 is of that size
+// too).  The scale 2^15 keeps P' in the normal FP16 range down to P = 2^-29.  The V tile
+// has max(16, 2R) rows (Vh of every q, Vl of every q, then zero rows): N is at least 16.  The fold
+// warps read C after every column tile, add its two halves, sum in FP32 over 16 tiles and
+// in FP64 beyond, and write the item's partial sums scaled back by 2^-(15 + e_q).
+// Roles: warp 0 lane 0 copies, warp 1 lane 0 issues MMAs, warps 2..13 are three groups of
+// four that exponentiate every third 128 x 64 unit, warps 14..21 fold C (four per half).
+constexpr int PV_BN = 128;        // columns per column tile
+constexpr int PV_ROWS = 256;      // rows per work item (two 128-row halves)
+constexpr int PV_GROUPS = 3;
+constexpr int PV_THREADS = 32 * (2 + 4 * PV_GROUPS + 8);
+constexpr int PV_UC = 64;          // columns per unit (two units per half per column tile)
+constexpr int PV_NBUF = 6;         // S/P buffers of 64 TMEM columns, two per group
+constexpr int PV_LOOK = 3;         // exponent MMAs issued ahead of the P.V MMAs
+constexpr int PV_FOLD = 16;        // column tiles summed in FP32 before the FP64 fold
+constexpr int PV_NSMAX = 4;        // most column-tile stages
+constexpr uint32_t PV_CCOL = PV_NBUF * PV_UC;   // first C column (4 buffers of 32 after it)
+static_assert(PV_NBUF == 2 * PV_GROUPS && PV_LOOK + PV_GROUPS <= PV_NBUF,
+              "an exponent MMA issued ahead must find its buffer already consumed");
+static_assert(PV_CCOL + 4 * 32 <= 512, "TMEM columns");
+
+struct PvShared {
+    uint64_t a_full, a_empty, s_full[PV_NSMAX], s_empty[PV_NSMAX], x_full[PV_NBUF], x_empty[PV_NBUF],
+        p_full[PV_NBUF], c_full[4], c_empty[4], drain;
+    uint32_t tbase;
+    int abort;
+};
+
+// The problems of one launch: a device table (grouped) or a single problem by value.
+struct PvWork {
+    const PvProb* table;
+    int nprob;
+    PvProb one;
+};
+// Where item `item` works; `pc` is the running problem index of the caller, which visits
+// items in increasing order.
+struct PvItem {
+    const PvProb* pb;
+    int rb, sp, t0, t1;
+    uint32_t tileA;
+};
+__device__ __forceinline__ PvItem pv_item(const PvWork& w, int item, int& pc) {
+    PvItem it;
+    if (w.table) {
+        while (pc + 1 < w.nprob && item >= w.table[pc + 1].item0) ++pc;
+        it.pb = &w.table[pc];
+    } else {
+        it.pb = &w.one;
+    }
+    const PvProb& pb = *it.pb;
+    const int li = item - pb.item0;
+    it.rb = li / pb.splits;
+    it.sp = li - it.rb * pb.splits;
+    it.t0 = it.sp * pb.tps;
+    it.t1 = min(it.t0 + pb.tps, (pb.nc + PV_BN - 1) / PV_BN);
+    it.tileA = 128u * (uint32_t)pb.Kp * 2u;
+    return it;
+}
+
+// Walks the (item, column tile, unit) sequence of one CTA; U counts units, T tiles and
+// ic items, in the same order for every role.
+struct PvCursor {
+    PvItem it;
+    int item, t, u, pc;
+    uint32_t U, T, ic;
+    bool valid;
+    __device__ void set_item(const PvWork& w, int i, int items) {
+        item = i;
+        valid = i < items;
+        if (valid) {
+            it = pv_item(w, i, pc);
+            t = it.t0;
+        }
+    }
+    __device__ void advance(const PvWork& w, int items) {
+        ++U;
+        if (++u == 4) {
+            u = 0;
+            ++T;
+            if (++t == it.t1) {
+                ++ic;
+                set_item(w, item + (int)gridDim.x, items);
+            }
+        }
+    }
+};
+
+// 2^15 2^t for two neighbouring columns, as FP16 pairs hi (Ph) and lo (Pl = P' - Ph rounded)
+__device__ __forceinline__ void pv_split2(uint32_t t0, uint32_t t1, uint32_t& hi, uint32_t& lo) {
+    const float p0 = ex2f(__uint_as_float(t0)) * 32768.f;
+    const float p1 = ex2f(__uint_as_float(t1)) * 32768.f;
+    hi = pack_f16x2(p0, p1);
+    float r0, r1;
+    // r = P' - Ph exactly (Ph is within 2^-11 of P'): one mixed FP16 x FP16 + FP32 FMA each
+    asm("{\n .reg .b16 h0, h1, m1;\n mov.b32 {h0, h1}, %2;\n mov.b16 m1, 0xBC00;\n"
+        " fma.rn.f32.f16 %0, h0, m1, %3;\n fma.rn.f32.f16 %1, h1, m1, %4;\n}"
+        : "=f"(r0), "=f"(r1)
+        : "r"(hi), "f"(p0), "f"(p1));
+    lo = pack_f16x2(r0, r1);
+}
+
+// stage = bytes of one column-tile stage (features of the widest problem, then V), abytes =
+// bytes of the row operand region (two tiles of the widest problem).
+template <int NRHS>
+__global__ void __launch_bounds__(PV_THREADS, 1)
+k_kmvm_tcpv(const __grid_constant__ PvWork w, int items, int ns, uint32_t stage, uint32_t abytes,
+            int* __restrict__ err, long long wlimit, int stall_copies) {
+    static_assert(NRHS == 1 || NRHS == 2 || NRHS == 4 || NRHS == 8 || NRHS == 16, "right-hand sides");
+    constexpr uint32_t VROWS = 2 * NRHS < 16 ? 16 : 2 * NRHS;   // Vh rows, Vl rows, zero rows
+    constexpr uint32_t VSLAB = VROWS * 128u;          // bytes of 64 K of the V tile
+    constexpr uint32_t VBYTES = 2 * VSLAB;            // one 128-column V tile
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t vstage = stage - VBYTES;           // offset of V inside a stage
+    unsigned char* sA = smem;                         // 256 rows
+    unsigned char* sB = smem + abytes;                // ns stages: column features, then V
+    double* sAcc = reinterpret_cast<double*>(sB + (size_t)ns * stage);   // [NRHS][256] FP64 sums
+    PvShared* sh = reinterpret_cast<PvShared*>(sAcc + NRHS * 256);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&sh->a_full, 1);
+        mbar_init(&sh->a_empty, 1);
+        for (int s = 0; s < PV_NSMAX; ++s) {
+            mbar_init(&sh->s_full[s], 1);
+            mbar_init(&sh->s_empty[s], 1);
+        }
+        for (int b = 0; b < PV_NBUF; ++b) {
+            mbar_init(&sh->x_full[b], 1);
+            mbar_init(&sh->x_empty[b], 1);
+            mbar_init(&sh->p_full[b], 4);
+        }
+        for (int c = 0; c < 4; ++c) {
+            mbar_init(&sh->c_full[c], 1);
+            mbar_init(&sh->c_empty[c], 4);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) tmem_alloc(&sh->tbase, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tbase;
+    volatile int* abort = &sh->abort;
+    auto give_up = [&]() {
+        *abort = 1;
+        atomicExch(err, 1);
+    };
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t T = 0, ic = 0;
+            int pc = 0;
+            for (int item = blockIdx.x; item < items && !*abort && !stall_copies; item += gridDim.x) {
+                const PvItem it = pv_item(w, item, pc);
+                const uint32_t tileA = it.tileA;
+                if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u, wlimit)) { give_up(); break; }
+                mbar_expect_tx(&sh->a_full, 2 * tileA);
+                bulk_g2s(sA, it.pb->FA + (size_t)it.rb * 2 * tileA, 2 * tileA, &sh->a_full);
+                ++ic;
+                bool ok = true;
+                for (int t = it.t0; t < it.t1; ++t) {
+                    const int s = (int)(T % (uint32_t)ns);
+                    if (!mbar_wait(&sh->s_empty[s], ((T / ns) & 1u) ^ 1u, wlimit)) { ok = false; break; }
+                    mbar_expect_tx(&sh->s_full[s], tileA + VBYTES);
+                    bulk_g2s(sB + (size_t)s * stage, it.pb->FB + (size_t)t * tileA, tileA, &sh->s_full[s]);
+                    bulk_g2s(sB + (size_t)s * stage + vstage, it.pb->Vt + (size_t)t * VBYTES, VBYTES,
+                             &sh->s_full[s]);
+                    ++T;
+                }
+                if (!ok) { give_up(); break; }
+            }
+            // drain: one arrival per barrier phase, so a parity wait on the newest is exact
+            for (uint32_t i = 0; i < (T < (uint32_t)ns ? T : (uint32_t)ns); ++i) {
+                const uint32_t gg = T - 1 - i;
+                mbar_wait(&sh->s_full[gg % ns], (gg / ns) & 1u, wlimit);
+            }
+            if (ic > 0) mbar_wait(&sh->a_full, (ic - 1) & 1u, wlimit);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id_exp = idesc_bf16(128, PV_UC);
+            const uint32_t id_hi = idesc_f16(128, VROWS), id_lo = idesc_f16(128, 16);
+            PvCursor e{}, p{};
+            e.set_item(w, blockIdx.x, items);
+            p.set_item(w, blockIdx.x, items);
+            bool issued = false, ok = true;
+            auto exp_mma = [&](const PvCursor& c) -> bool {
+                if (c.u == 0 && c.t == c.it.t0 && !mbar_wait(&sh->a_full, c.ic & 1u, wlimit)) return false;
+                const int s = (int)(c.T % (uint32_t)ns);
+                if (c.u == 0 && !mbar_wait(&sh->s_full[s], (c.T / ns) & 1u, wlimit)) return false;
+                const int b = (int)(c.U % PV_NBUF);
+                if (!mbar_wait(&sh->x_empty[b], ((c.U / PV_NBUF) & 1u) ^ 1u, wlimit)) return false;
+                tc_fence_after();
+                const int h = c.u >> 1, cc = c.u & 1;
+                const uint32_t a_addr = smem_u32(sA) + (uint32_t)h * c.it.tileA;
+                // columns 64 cc .. 64 cc + 63 of the tile: rows 64 cc.. of every K slab
+                const uint32_t b_addr = smem_u32(sB + (size_t)s * stage) + (uint32_t)cc * 8192u;
+                for (int kk = 0; kk < c.it.pb->Kp / 16; ++kk) {
+                    const uint32_t koff = (uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u;
+                    mma_bf16(tmem + (uint32_t)(b * PV_UC), smem_desc_sw128(a_addr + koff),
+                             smem_desc_sw128(b_addr + koff), id_exp, kk > 0 ? 1u : 0u);
+                }
+                mma_commit(&sh->x_full[b]);
+                if (c.u == 3 && c.t == c.it.t1 - 1) mma_commit(&sh->a_empty);   // last use of the rows
+                issued = true;
+                return true;
+            };
+            auto pv_mma = [&](const PvCursor& c) -> bool {
+                const int b = (int)(c.U % PV_NBUF);
+                if (!mbar_wait(&sh->p_full[b], (c.U / PV_NBUF) & 1u, wlimit)) return false;
+                const int h = c.u >> 1, cc = c.u & 1;
+                const int ci = 2 * h + (int)(c.T & 1u);
+                if (cc == 0 && !mbar_wait(&sh->c_empty[ci], ((c.T >> 1) & 1u) ^ 1u, wlimit)) return false;
+                tc_fence_after();
+                const int s = (int)(c.T % (uint32_t)ns);
+                const uint32_t v_addr = smem_u32(sB + (size_t)s * stage + vstage) + (uint32_t)cc * VSLAB;
+                const uint32_t d = tmem + PV_CCOL + 32u * ci;
+                const uint32_t pb = tmem + (uint32_t)(b * PV_UC);
+                for (int kk = 0; kk < PV_UC / 16; ++kk) {
+                    const uint32_t a_hi = pb + 32u * (kk >> 1) + 8u * (kk & 1);
+                    const uint64_t bd = smem_desc_sw128(v_addr + 32u * kk);
+                    mma_f16_ts(d, a_hi, bd, id_hi, (cc > 0 || kk > 0) ? 1u : 0u);
+                    mma_f16_ts(d, a_hi + 16u, bd, id_lo, 1u);
+                }
+                mma_commit(&sh->x_empty[b]);
+                if (cc == 1) mma_commit(&sh->c_full[ci]);
+                if (c.u == 3) mma_commit(&sh->s_empty[s]);
+                return true;
+            };
+            for (int i = 0; i < PV_LOOK && e.valid && ok; ++i) {
+                ok = exp_mma(e);
+                e.advance(w, items);
+            }
+            while (ok && p.valid && !*abort) {
+                if (e.valid) {
+                    ok = exp_mma(e);
+                    e.advance(w, items);
+                    if (!ok) break;
+                }
+                ok = pv_mma(p);
+                p.advance(w, items);
+            }
+            if (!ok) give_up();
+            if (issued) {   // every MMA issued has finished once the drain phase completes
+                mma_commit(&sh->drain);
+                mbar_wait(&sh->drain, 0, wlimit);
+            }
+        }
+    } else if (warp < 2 + 4 * PV_GROUPS) {
+        // ---------------------------------------------------------- exponentials
+        const int grp = (warp - 2) >> 2, quarter = warp & 3;
+        uint32_t total = 0;
+        int pc = 0;
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+            const PvItem it = pv_item(w, item, pc);
+            total += 4u * (uint32_t)(it.t1 - it.t0);
+        }
+        for (uint32_t U = grp; U < total && !*abort; U += PV_GROUPS) {
+            const int b = (int)(U % PV_NBUF);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&sh->x_full[b], (U / PV_NBUF) & 1u, wlimit));
+            if (!ok) { if (lane == 0) give_up(); break; }
+            tc_fence_after();
+            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * PV_UC);
+#pragma unroll 1
+            for (int c32 = 0; c32 < PV_UC / 32; ++c32) {
+                uint32_t r[32], o[32];
+                tmem_ld32(tb + 32u * c32, r);
+                tmem_wait_ld(r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pv_split2(r[2 * j], r[2 * j + 1], o[j], o[16 + j]);
+                tmem_st32(tb + 32u * c32, o);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->p_full[b]);
+        }
+    } else {
+        // ---------------------------------------------------------- fold
+        const int f = warp - 2 - 4 * PV_GROUPS;       // 0..7
+        const int h = f >> 2, quarter = warp & 3;
+        const int lrow = h * 128 + quarter * 32 + lane;
+        uint32_t T = 0;
+        int pc = 0;
+        for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
+            const PvItem it = pv_item(w, item, pc);
+            const int t0 = it.t0, t1 = it.t1;
+            float acc[NRHS];
+#pragma unroll
+            for (int q = 0; q < NRHS; ++q) {
+                acc[q] = 0.f;
+                sAcc[q * 256 + lrow] = 0.0;
+            }
+            bool ok = true;
+            int nf = 0;
+            for (int t = t0; t < t1; ++t, ++T) {
+                const int ci = 2 * h + (int)(T & 1u);
+                ok = __all_sync(0xffffffffu, mbar_wait(&sh->c_full[ci], (T >> 1) & 1u, wlimit));
+                if (!ok) { if (lane == 0) give_up(); break; }
+                tc_fence_after();
+                const uint32_t ca = tmem + ((uint32_t)(quarter * 32) << 16) + PV_CCOL + 32u * ci;
+                if constexpr (NRHS == 16) {
+                    uint32_t c[32];
+                    tmem_ld32(ca, c);
+                    tmem_wait_ld(c);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->c_empty[ci]);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[q] += __uint_as_float(c[q]) + __uint_as_float(c[16 + q]);
+                } else {
+                    uint32_t c[16];
+                    tmem_ld16(ca, c);
+                    tmem_wait_ld16(c);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->c_empty[ci]);
+#pragma unroll
+                    for (int q = 0; q < NRHS; ++q)
+                        acc[q] += __uint_as_float(c[q]) + __uint_as_float(c[NRHS + q]);
+                }
+                if (++nf == PV_FOLD || t == t1 - 1) {
+#pragma unroll
+                    for (int q = 0; q < NRHS; ++q) {
+                        sAcc[q * 256 + lrow] += (double)acc[q];
+                        acc[q] = 0.f;
+                    }
+                    nf = 0;
+                }
+            }
+            if (!ok) break;
+            const long long row = (long long)it.rb * PV_ROWS + lrow;
+            const int nr = it.pb->nr;
+            if (row < nr) {
+                double* part = it.pb->part;
+                const double* vsc = it.pb->vsc;
+#pragma unroll
+                for (int q = 0; q < NRHS; ++q)
+                    part[((size_t)it.sp * NRHS + q) * nr + row] = sAcc[q * 256 + lrow] * vsc[q];
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// Per right-hand side q of V (ldv-strided columns, n entries): e_q = 15 - (binary exponent
+// of max |V_q|) so that 2^e_q max |V_q| lies in [2^14, 2^15) (0 when the column is zero or
+// not finite); vexp[q] = e_q and vsc[q] = 2^-(15 + e_q), the factor that undoes both scales.
+__global__ void k_pv_vscale(const float* __restrict__ V, int ldv, int n, int* __restrict__ vexp,
+                            double* __restrict__ vsc) {
+    __shared__ float red[32];
+    const int q = blockIdx.x;
+    float m = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, fabsf(V[(size_t)q * ldv + j]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        m = warp_max(m);
+        if (threadIdx.x == 0) {
+            int ex = 0;
+            const bool ok = m > 0.f && m <= 3.4028234663852886e38f;
+            if (ok) frexpf(m, &ex);
+            const int e = ok ? 15 - ex : 0;
+            vexp[q] = e;
+            vsc[q] = ldexp(1.0, -(15 + e));
+        }
+    }
+}
+
+// V' = 2^e_q V split as Vh + Vl (FP16, round to nearest) into 128-column tiles of
+// rows = max(16, 2R) rows (Vh of every q, then Vl, then zeros) in the 128-byte swizzled
+// K-major layout, zero beyond n.  One thread per (row, column).
+__global__ void k_pv_vsplit(const float* __restrict__ V, int ldv, int n, int ncp, int nrhs, int rows,
+                            const int* __restrict__ vexp, unsigned char* __restrict__ Vt) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * ncp) return;
+    const int r = (int)(e / ncp), j = (int)(e - (long long)r * ncp);
+    const int q = r < nrhs ? r : r - nrhs;
+    float out = 0.f;
+    if (r < 2 * nrhs && j < n) {
+        const float v = ldexpf(V[(size_t)q * ldv + j], vexp[q]);
+        const float hv = __half2float(__float2half_rn(v));
+        out = r < nrhs ? hv : v - hv;
+    }
+    unsigned char* tile = Vt + (size_t)(j >> 7) * ((size_t)rows * 256u);
+    *reinterpret_cast<__half*>(tile + tile_off_sw(r, j & 127, rows)) = __float2half_rn(out);
 }
 
 // ------------------------------------------------------------------ tensor-core sketch
@@ -808,8 +1305,155 @@ size_t tc_feature_bytes(long long n, int d) {
 }
 
 typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
-                      int, int, int, double*, int*, long long, int);
+                      int, int, int, int, double*, int*, long long, int);
 
+
+// ---- grouped form: the same kernels over the problems of a batch, one launch each
+// Per (problem, right-hand side) block: the column's scale exponent, as k_pv_vscale.
+__global__ void k_pv_vscale_g(const PvPrep* __restrict__ tab, int nrhs) {
+    __shared__ float red[32];
+    const PvPrep& pp = tab[blockIdx.x / nrhs];
+    const int q = blockIdx.x % nrhs;
+    float m = 0.f;
+    for (int j = threadIdx.x; j < pp.n; j += blockDim.x) m = fmaxf(m, fabsf(pp.V[(size_t)q * pp.ldv + j]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        m = warp_max(m);
+        if (threadIdx.x == 0) {
+            int ex = 0;
+            const bool ok = m > 0.f && m <= 3.4028234663852886e38f;
+            if (ok) frexpf(m, &ex);
+            const int e = ok ? 15 - ex : 0;
+            pp.vexp[q] = e;
+            pp.vsc[q] = ldexp(1.0, -(15 + e));
+        }
+    }
+}
+
+// The split of every problem's V into its tiles, as k_pv_vsplit; blocks blk0 .. of problem p.
+__global__ void k_pv_vsplit_g(const PvPrep* __restrict__ tab, int nprob, int nrhs, int rows) {
+    int lo = 0, hi = nprob - 1;   // last problem whose first block is <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].blk0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const PvPrep& pp = tab[lo];
+    const long long e = (long long)((int)blockIdx.x - pp.blk0) * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * pp.ncp) return;
+    const int r = (int)(e / pp.ncp), j = (int)(e - (long long)r * pp.ncp);
+    const int q = r < nrhs ? r : r - nrhs;
+    float out = 0.f;
+    if (r < 2 * nrhs && j < pp.n) {
+        const float v = ldexpf(pp.V[(size_t)q * pp.ldv + j], pp.vexp[q]);
+        const float hv = __half2float(__float2half_rn(v));
+        out = r < nrhs ? hv : v - hv;
+    }
+    unsigned char* tile = pp.Vt + (size_t)(j >> 7) * ((size_t)rows * 256u);
+    *reinterpret_cast<__half*>(tile + tile_off_sw(r, j & 127, rows)) = __float2half_rn(out);
+}
+
+int pv_tile_bytes(int nrhs) { return std::max(16, 2 * nrhs) * PV_BN * 2; }
+
+int launch_pv_prep_grouped(krr_ctx* ctx, const PvPrep* tab_dev, int nprob, int nblk, int nrhs) {
+    k_pv_vscale_g<<<nprob * nrhs, 512, 0, ctx->stream>>>(tab_dev, nrhs);
+    KRR_CHECK_LAUNCH();
+    k_pv_vsplit_g<<<nblk, 256, 0, ctx->stream>>>(tab_dev, nprob, nrhs, std::max(16, 2 * nrhs));
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+// One launch of the product over the items of every problem in the device table (item0
+// prefix, `items` in all); kp_max is the widest feature row of any of them.
+int launch_kmvm_tcpv_table(krr_ctx* ctx, const PvProb* table_dev, int nprob, int items, int nrhs,
+                           int kp_max, int* err) {
+    const size_t vbytes = (size_t)pv_tile_bytes(nrhs);
+    const uint32_t tileA = 128u * kp_max * 2u;
+    int optin = 0;
+    KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    const size_t fixed = 2 * (size_t)tileA + (size_t)256 * nrhs * 8 + sizeof(PvShared) + 1024;
+    const size_t stage = tileA + vbytes;
+    const int ns = (int)std::min<size_t>(PV_NSMAX, (size_t)optin > fixed ? ((size_t)optin - fixed) / stage : 0);
+    if (ns < 2) return fail(ctx, KRR_E_INVAL, "tensor-core product: features too wide for the P.V form");
+    const size_t smem_launch = std::max<size_t>(fixed + ns * stage, 120 * 1024);
+    auto fn = nrhs == 16 ? &k_kmvm_tcpv<16> : nrhs == 8 ? &k_kmvm_tcpv<8> : nrhs == 4 ? &k_kmvm_tcpv<4>
+            : nrhs == 2 ? &k_kmvm_tcpv<2> : &k_kmvm_tcpv<1>;
+    KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
+    const long long wlimit = ctx->opts.wait_limit_log2 > 0 ? (1LL << ctx->opts.wait_limit_log2)
+                                                           : kWaitLimitDefault;
+    PvWork w{};
+    w.table = table_dev;
+    w.nprob = nprob;
+    const int grid = std::min(items, ctx->num_sms);
+    fn<<<grid, PV_THREADS, smem_launch, ctx->stream>>>(w, items, ns, (uint32_t)stage, 2u * tileA, err, wlimit,
+                                                       ctx->opts.test_stall_copies);
+    KRR_CHECK_LAUNCH();
+    return KRR_OK;
+}
+
+// Q = K(rows, cols) V + beta V for 8 or 16 right-hand sides with P.V on the tensor cores.
+static int launch_kmvm_tcpv(krr_ctx* ctx, const unsigned char* FA, long long nr, const unsigned char* FB,
+                            long long nc, int Kp, float beta, const float* V, int nrhs, float* Q, int* err) {
+    const int ncp = (int)((nc + PV_BN - 1) / PV_BN * PV_BN);
+    const int vrows = std::max(16, 2 * nrhs);
+    const size_t vbytes = (size_t)vrows * PV_BN * 2;        // one V tile: Vh, Vl (and zeros), FP16
+    unsigned char* Vt;
+    int* vexp;
+    double* vsc;
+    KRR_RET(bufT(ctx, "pv_vt", vbytes * (ncp / PV_BN), &Vt));
+    KRR_RET(bufT(ctx, "pv_vexp", 16, &vexp));
+    KRR_RET(bufT(ctx, "pv_vsc", 16, &vsc));
+    k_pv_vscale<<<nrhs, 512, 0, ctx->stream>>>(V, (int)nc, (int)nc, vexp, vsc);
+    KRR_CHECK_LAUNCH();
+    const long long nsplit = (long long)vrows * ncp;
+    k_pv_vsplit<<<ceil_div(nsplit, 256), 256, 0, ctx->stream>>>(V, (int)nc, (int)nc, ncp, nrhs, vrows, vexp, Vt);
+    KRR_CHECK_LAUNCH();
+    const uint32_t tileA = 128u * Kp * 2u;
+    const size_t fixed = 2 * (size_t)tileA + (size_t)256 * nrhs * 8 + sizeof(PvShared) + 1024;
+    const size_t stage = tileA + vbytes;
+    int optin = 0;
+    KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    const size_t cap = (size_t)optin;
+    const int ns = (int)std::min<size_t>(PV_NSMAX, cap > fixed ? (cap - fixed) / stage : 0);
+    if (ns < 2) return fail(ctx, KRR_E_INVAL, "tensor-core product: features too wide for the P.V form");
+    const size_t smem = fixed + ns * stage;
+    const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
+    auto fn = nrhs == 16 ? &k_kmvm_tcpv<16> : nrhs == 8 ? &k_kmvm_tcpv<8> : nrhs == 4 ? &k_kmvm_tcpv<4>
+            : nrhs == 2 ? &k_kmvm_tcpv<2> : &k_kmvm_tcpv<1>;
+    KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
+    const int nrb = (int)ceil_div(nr, PV_ROWS);
+    const int ntiles = ncp / PV_BN;
+    int splits = 1;
+    long long best = -1;
+    for (int sc = 1; sc <= std::min(64, ntiles); ++sc) {   // as in launch_kmvm_tc
+        const long long per = (ntiles + sc - 1) / sc;
+        const long long waves = ((long long)nrb * sc + ctx->num_sms - 1) / ctx->num_sms;
+        const long long cost = waves * (per + 8);
+        if (best < 0 || cost < best) {
+            best = cost;
+            splits = sc;
+        }
+    }
+    const int tps = (ntiles + splits - 1) / splits;
+    splits = (ntiles + tps - 1) / tps;
+    const int items = nrb * splits;
+    double* part;
+    KRR_RET(bufT(ctx, "tc_part", (size_t)splits * nrhs * nr, &part));
+    const int grid = std::min(items, ctx->num_sms);
+    const long long wlimit = ctx->opts.wait_limit_log2 > 0 ? (1LL << ctx->opts.wait_limit_log2)
+                                                           : kWaitLimitDefault;
+    PvWork w{};
+    w.table = nullptr;
+    w.nprob = 1;
+    w.one = PvProb{FA, FB, Vt, vsc, part, (int)nr, (int)nc, Kp, splits, tps, items, 0, 0};
+    fn<<<grid, PV_THREADS, smem_launch, ctx->stream>>>(w, items, ns, (uint32_t)stage, 2u * tileA, err, wlimit,
+                                                       ctx->opts.test_stall_copies);
+    KRR_CHECK_LAUNCH();
+    return launch_kmvm_reduce(ctx, part, splits, (int)nr, nrhs, V, (int)nc, beta, Q, (int)nr);
+}
 
 // Q = K(rows, cols) V + beta V using features FA (rows) and FB (cols).
 int launch_kmvm_reduce64(krr_ctx* ctx, const double* part, int nparts, int nr, int nrhs2,
@@ -832,17 +1476,29 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
     while (done < nrhs) {
         const int left = nrhs - done;
         const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+        if (!hp && (ctx->opts.tc_pv == 2 || (ctx->opts.tc_pv == 1 && chunk >= 8))) {
+            KRR_RET(launch_kmvm_tcpv(ctx, FA, nr, FB, nc, Kp, beta, V + (size_t)done * nc, chunk,
+                                     Q + (size_t)done * nr, err));
+            done += chunk;
+            continue;
+        }
         tc_fn fn = chunk == 1 ? &k_kmvm_tc<1> : chunk == 2 ? &k_kmvm_tc<2> : chunk == 4 ? &k_kmvm_tc<4>
                  : chunk == 8 ? &k_kmvm_tc<8> : &k_kmvm_tc<16>;
-        // V padded to whole 128-column tiles, RHS-major (16-byte aligned bulk copies)
+        // V padded to whole 256-column tiles, RHS-major (16-byte aligned bulk copies)
         float* Vp;
         KRR_RET(bufT(ctx, "tc_vpad", (size_t)chunk * ncp, &Vp));
         KRR_TRY_CUDA(cudaMemsetAsync(Vp, 0, sizeof(float) * chunk * ncp, ctx->stream));
         KRR_TRY_CUDA(cudaMemcpy2DAsync(Vp, sizeof(float) * ncp, V + (size_t)done * nc, sizeof(float) * nc,
                                        sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
         const uint32_t tileA = 128u * Kp * 2u;
-        const size_t smem = (2 + TC_NS) * (size_t)tileA + (size_t)TC_NS * chunk * TC_BN * 4 + 256;
-        const size_t smem_launch = std::max<size_t>(smem + 1024, 120 * 1024);   // one CTA per SM (TMEM)
+        // stages: four where they fit (K = 64), else two
+        int optin = 0;
+        KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        const size_t stage = 2 * (size_t)tileA + (size_t)chunk * TC_BN * 4;
+        const size_t fixed = (size_t)tileA + sizeof(TcShared) + 1024;
+        const int ns = fixed + 4 * stage <= (size_t)optin ? 4 : 2;
+        if (fixed + ns * stage > (size_t)optin) return fail(ctx, KRR_E_INVAL, "tensor-core product: tiles too wide");
+        const size_t smem_launch = std::max<size_t>(fixed + ns * stage, 120 * 1024);   // one CTA per SM (TMEM)
         KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
         const int nrb = (int)ceil_div(nr, TC_ROWS);
         const int ntiles = ncp / TC_BN;
@@ -863,20 +1519,20 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         splits = (ntiles + tps - 1) / tps;
         const int items = nrb * splits;
         double* part;
-        KRR_RET(bufT(ctx, "tc_part", (size_t)2 * splits * chunk * nr, &part));
+        KRR_RET(bufT(ctx, "tc_part", (size_t)4 * splits * chunk * nr, &part));
         const int grid = std::min(items, ctx->num_sms);
         const long long wlimit = ctx->opts.wait_limit_log2 > 0 ? (1LL << ctx->opts.wait_limit_log2)
                                                                : kWaitLimitDefault;
         fn<<<grid, TC_THREADS, smem_launch, ctx->stream>>>(FA, FB, Kp, (int)nr, (int)nc, ncp, Vp, items,
-                                                           splits, tps, part, err, wlimit,
+                                                           splits, tps, ns, part, err, wlimit,
                                                            ctx->opts.test_stall_copies);
         KRR_CHECK_LAUNCH();
-        // two column groups per split: 2 * splits partial sums per output
+        // four column groups (tile parity x column half) per split: 4 * splits partial sums
         if (hp)
-            KRR_RET(launch_kmvm_reduce64(ctx, part, 2 * splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
+            KRR_RET(launch_kmvm_reduce64(ctx, part, 4 * splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
                                          (double)beta, Q64 + (size_t)(done / 2) * nr, ex2_bias_scale(ctx)));
         else
-            KRR_RET(launch_kmvm_reduce(ctx, part, 2 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
+            KRR_RET(launch_kmvm_reduce(ctx, part, 4 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
                                        beta, Q + (size_t)done * nr, (int)nr));
         done += chunk;
     }
@@ -889,7 +1545,7 @@ using namespace krr;
 
 // Known-answer test of the tcgen05 descriptor encodings (host entry, see krr.h).
 extern "C" int krr_tc_selftest(int variant, int* mismatches, float* max_err, void* stream_v) {
-    if (!mismatches || !max_err || variant < 0 || variant > 3) return KRR_E_INVAL;
+    if (!mismatches || !max_err || variant < 0 || variant > 4) return KRR_E_INVAL;
     cudaStream_t stream = (cudaStream_t)stream_v;
     float* out = nullptr;
     int* err = nullptr;

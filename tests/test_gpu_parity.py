@@ -116,6 +116,8 @@ def test_tc_descriptor_known_answer():
     assert bad2 == 0 and err2 == 0.0
     bad3, _ = api.tc_selftest(3)   # the same data through an unswizzled descriptor
     assert bad3 > 0
+    bad4, err4 = api.tc_selftest(4)   # FP16, A from tensor memory (the P.V step)
+    assert bad4 == 0 and err4 == 0.0
 
 
 @pytest.mark.parametrize("n,d,nrhs,beta", [(2000, 4, 1, 1e-2), (1, 3, 1, 0.5), (127, 2, 3, 0.0),
@@ -130,6 +132,46 @@ def test_kmvm_tensor_core_square(K, n, d, nrhs, beta):
     Q = ctx.kmvm(_t(X), _t(X), _t(V), sigma, beta).cpu().numpy()
     ref = O.kmvm(X, V.astype(np.float64), sigma, beta)
     assert _relcols(Q, ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("nr,nc,d,nrhs,scaled", [(3000, 3000, 3, 16, False), (2500, 4099, 8, 8, False),
+                                                  (1000, 777, 13, 16, True), (5000, 5000, 16, 8, True),
+                                                  (1, 300, 4, 16, False), (4099, 4099, 8, 1, False),
+                                                  (3000, 2000, 5, 4, True), (700, 700, 2, 2, False)])
+def test_kmvm_tensor_core_pv_on_tensor_cores(K, nr, nc, d, nrhs, scaled):
+    # P V contracted on the tensor cores (FP16 hi + lo parts of P and of the per-column
+    # rescaled V; the default for blocks of 8 or 16 right-hand sides, tc_pv = 2 for fewer):
+    # several column tiles and splits, a ragged tail, rectangular shapes, columns spanning
+    # 10^-30 .. 10^25 and a zero column
+    rng = np.random.Generator(np.random.PCG64(nr + 7 * nc + d))
+    Xc = rng.uniform(-2, 2, size=(nc, d)).astype(np.float32)
+    Xr = Xc[:nr] if nr <= nc else rng.uniform(-2, 2, size=(nr, d)).astype(np.float32)
+    if nr != nc:
+        Xr = Xr + np.float32(0.05)
+    V = rng.normal(size=(nc, nrhs)).astype(np.float32)
+    if scaled:
+        V *= (10.0 ** np.linspace(-30, 25, nrhs)).astype(np.float32)
+        V[:, nrhs - 2] = 0.0
+    sigma = 0.3 * np.sqrt(d)
+    beta = 1e-3 if nr == nc else 0.0
+    V64 = V.astype(np.float64)
+    ref = O.kmvm(Xc, V64, sigma, beta) if nr == nc else O.kmvm_rect(Xr, Xc, V64, sigma)
+    mag = O.kmvm_rect(Xr, Xc, np.abs(V64), sigma)                 # sum of |terms|
+    if nr == nc:
+        mag += beta * np.abs(V64)
+    nz = np.abs(V).max(axis=0) > 0
+    Qs = {}
+    on = 1 if nrhs >= 8 else 2
+    for tc_pv in (on, 0):
+        Q = K(precision=1, tc_pv=tc_pv).kmvm(_t(Xr), _t(Xc), _t(V), sigma, beta).cpu().numpy()
+        assert np.all(Q[:, ~nz] == 0.0)
+        if nr >= 64:   # (one row that cancels has no meaningful column norm)
+            assert _relcols(Q[:, nz], ref[:, nz]).max() <= 1e-5
+        assert (np.abs(Q[:, nz] - ref[:, nz]) / mag[:, nz]).max() <= 3e-5
+        Qs[tc_pv] = Q
+    # both forms share the exponents; the P V arithmetic alone (FP16 hi + lo parts, 22
+    # bits, against FP32 products) moves every output by a few 2^-22 of its |terms| at most
+    assert (np.abs(Qs[on][:, nz] - Qs[0][:, nz]) / mag[:, nz]).max() <= 3e-6
 
 
 def test_kmvm_tensor_core_square_full_size_sampled_rows(K):

@@ -22,10 +22,12 @@ def _case(n=3000, d=6, nrhs=2, seed=31):
     return X, V
 
 
-def test_stalled_tensor_core_product_times_out_and_reports_it():
+@pytest.mark.parametrize("nrhs", [2, 16])
+def test_stalled_tensor_core_product_times_out_and_reports_it(nrhs):
+    # nrhs = 16 runs the product with P.V on the tensor cores (its own kernel and waits)
     from paper_1905_10587_gb300 import _lib
     from paper_1905_10587_gb300.api import KRR, KRRError
-    X, V = _case()
+    X, V = _case(nrhs=nrhs)
     Xd, Vd = torch.from_numpy(X).cuda(), torch.from_numpy(V).cuda()
     ctx = KRR(precision=1, wait_limit_log2=20, test_stall_copies=1)
     with pytest.raises(KRRError) as ei:
