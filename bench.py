@@ -471,8 +471,9 @@ def _form_fma_ops(form: int, d: int, nrhs: int, tc_pv: bool = True) -> float:
 
 
 def batched_extra(api, sms: int, sm_hz: float, workers: int = 8) -> dict:
-    """The 64-problem batch (n log-uniform in [1e3, 5e4], d in 2..16, 8 RHS) through
-    krr_batch_solve, in the tensor-core form and in the plain FP32 form, each to 1e-6.
+    """The 64-problem batch (n log-uniform in [1e3, 5e4], d in 2..16, 8 RHS) to 1e-6: in lockstep
+    with one launch per step over all problems (krr_batch_solve_grouped, tensor-core form),
+    and one by one on worker threads (krr_batch_solve) in the tensor-core and FP32 forms.
     `frac` = (the batch's products timed at their ALU bounds) / (batch wall time)."""
     import torch
     import synth
@@ -483,11 +484,13 @@ def batched_extra(api, sms: int, sm_hz: float, workers: int = 8) -> dict:
     out = {"workload": "64 problems, n log-uniform [1e3, 5e4], d in 2..16, X ~ N(0, I), 8 RHS "
                        "sin(w.x), sigma = sqrt(d), beta = 1e-3, k = min(500, n/10), tol 1e-6",
            "workers": workers}
-    for prec, name in ((1, "tensor_core"), (0, "fp32")):
-        api.batch_solve(args_[:4], tol=1e-6, seed=1, workers=workers, precision=prec)
+    for prec, name, grouped in ((1, "tensor_core_grouped", True), (1, "tensor_core", False),
+                                (0, "fp32", False)):
+        api.batch_solve(args_[:4], tol=1e-6, seed=1, workers=workers, precision=prec, grouped=grouped)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, infos, stats = api.batch_solve(args_, tol=1e-6, seed=1, workers=workers, precision=prec)
+        _, infos, stats = api.batch_solve(args_, tol=1e-6, seed=1, workers=workers, precision=prec,
+                                          grouped=grouped)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         tmin = 0.0
@@ -550,11 +553,12 @@ def run_batched(args):
     probs = synth.batched()
     args_ = [(torch.from_numpy(p.X).cuda(), torch.from_numpy(p.Y).cuda(), p.sigma, p.beta, max(1, p.k))
              for p in probs]
-    api.batch_solve(args_[:4], tol=1e-6, seed=1, workers=args.workers, precision=args.precision)
+    api.batch_solve(args_[:4], tol=1e-6, seed=1, workers=args.workers, precision=args.precision,
+                    grouped=args.grouped)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     alphas, infos, stats = api.batch_solve(args_, tol=1e-6, seed=1, workers=args.workers,
-                                           precision=args.precision)
+                                           precision=args.precision, grouped=args.grouped)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     pairs = sum(float(p.n) ** 2 for p in probs)
@@ -563,7 +567,7 @@ def run_batched(args):
                       "config": {"workload": "64 problems, n log-uniform [1e3, 5e4], d in 2..16, "
                                  "X ~ N(0, I), 8 RHS sin(w.x), sigma = sqrt(d), beta = 1e-3, "
                                  "k = min(500, n/10)", "workers": args.workers,
-                                 "precision": args.precision},
+                                 "precision": args.precision, "grouped": args.grouped},
                       "converged": sum(1 for s in stats if s == 0), "sum_n": sum(p.n for p in probs),
                       "sum_n2_pairs": pairs, "iters_total": sum(i["iters"] for i in infos),
                       "max_rel_residual": max(max(i["rel_residual"]) for i in infos)}))
@@ -728,6 +732,8 @@ def main():
                     choices=["mixture", "batched", "gradient", "cube", "condition"])
     ap.add_argument("--cube-iters", type=int, default=300)
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--grouped", action="store_true",
+                    help="batched workload: lockstep solve with one launch per step over all problems")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -108,7 +108,11 @@ typedef struct krr_opts {
                              V as FP16 hi + lo pairs, about 2^-22 relative per entry;
                              FP32 V and Q only); 2: every block, 1 to 16 right-hand
                              sides; 0: P V as FP32 FMAs                                 */
-    int    reserved[3];
+    int    autotune;      /* 1: the kernel products take their column-split count (and
+                             the tensor-core product its P.V form) from the tuning table
+                             where it has an entry for the configuration (krr_autotune,
+                             krr_tune_load); 0 (default): from the cost model           */
+    int    reserved[2];
     double strong_f;      /* 0 (default): the build selects anchors by pivoted QR (Algorithm 1
                              step 3 as Section 3 remarks); f > 1: by strong RRQR with bound
                              f (Gu-Eisenstat; the factorization Eq. (4) assumes), see
@@ -411,6 +415,34 @@ int krr_batch_solve(const krr_problem* probs, int nprob, int nrhs, double tol, u
 int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int nrhs, double tol,
                             unsigned long long seed, const krr_opts* opts, int workers,
                             krr_solve_info* infos, int* statuses);
+
+/* ---------------------------------------------------------------------------
+ * Work-split tuning (no counterpart in the paper).  The kernel products split the
+ * columns of K into ranges handled by separate work items; the count comes from a
+ * cost model unless a tuning-table entry exists for the configuration and
+ * opts.autotune = 1.  Keys read "form=F w=W r=R lg=L": product form F (0 FP32
+ * expansion, 1 tensor cores, 2 exact differences), feature width W (tensor-core K,
+ * else the kernel dimension), R right-hand sides per launch, L = floor(log2 n).
+ * Entries hold the split count, the P.V form (1 = on tensor cores) and the time.
+ * The table is process-wide and guarded by a lock.
+ *
+ * krr_autotune: for the built problem of ctx, times the square product (the form of
+ * opts.precision) with nrhs in {1, 2, 4, 8, 16} right-hand sides for the cost model's
+ * choice and split counts 1 .. 64, and with 64-wide tensor-core features for both P.V
+ * forms; each candidate is run once to warm up, then reps times between CUDA events.
+ * Stores the fastest under its key and writes it to the host outputs (each may be NULL).
+ * KRR_E_STATE before a build, KRR_E_INVAL for a bad nrhs or reps outside 1 .. 100.
+ * krr_tune_save / krr_tune_load write and read the table as JSON (load adds entries;
+ * KRR_E_INVAL on a missing file or an entry that does not parse, with nothing added).
+ * krr_tune_get reads one entry (KRR_E_STATE when absent); krr_tune_set writes one;
+ * krr_tune_clear empties the table.
+ * ------------------------------------------------------------------------- */
+int krr_autotune(krr_ctx* ctx, int nrhs, int reps, int* splits, int* pv, double* ms);
+int krr_tune_save(const char* path);
+int krr_tune_load(const char* path);
+int krr_tune_get(const char* key, int* splits, int* pv, double* ms);
+int krr_tune_set(const char* key, int splits, int pv, double ms);
+int krr_tune_clear(void);
 
 #ifdef __cplusplus
 }

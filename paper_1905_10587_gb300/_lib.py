@@ -28,7 +28,7 @@ class KrrOpts(C.Structure):
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
                 ("escalate", C.c_int), ("sparse_r", C.c_int), ("wait_limit_log2", C.c_int),
                 ("test_stall_copies", C.c_int), ("no_precond", C.c_int), ("recurrence", C.c_int),
-                ("strong_swaps", C.c_int), ("ex2_correct", C.c_int), ("tc_pv", C.c_int), ("reserved", C.c_int * 3),
+                ("strong_swaps", C.c_int), ("ex2_correct", C.c_int), ("tc_pv", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int * 2),
                 ("strong_f", C.c_double)]
 
 
@@ -80,6 +80,12 @@ SIGNATURES = {
                              C.POINTER(KrrSolveInfo), C.POINTER(_i)]),
     "krr_batch_solve_grouped": (_i, [C.POINTER(KrrProblem), _i, _i, _d, _ull, C.POINTER(KrrOpts), _i,
                                      C.POINTER(KrrSolveInfo), C.POINTER(_i)]),
+    "krr_autotune": (_i, [_vp, _i, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
+    "krr_tune_save": (_i, [C.c_char_p]),
+    "krr_tune_load": (_i, [C.c_char_p]),
+    "krr_tune_get": (_i, [C.c_char_p, C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
+    "krr_tune_set": (_i, [C.c_char_p, _i, _i, _d]),
+    "krr_tune_clear": (_i, []),
     "krr_kmvm_dsigma": (_i, [_vp, _vp, _ll, _vp, _ll, _i, _d, _vp, _vp]),
     "krr_grad": (_i, [_vp, _vp, _vp, _ll, _vp, _d, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), _vp]),
     "krr_kmvm_noalloc": (_i, [_vp, _ll, _vp, _ll, _i, _d, _d, _vp, _i, _vp, _vp,

@@ -191,6 +191,13 @@ class KRR:
         self._check(self.lib.krr_anchor_stats(self.h, C.byref(sw), C.byref(rho)))
         return sw.value, rho.value
 
+    def autotune(self, nrhs: int = 1, reps: int = 3):
+        """Time the built problem's product for every candidate split (krr_autotune) and keep
+        the fastest in the process-wide tuning table; returns (splits, pv_form, ms)."""
+        sp, pv, ms = C.c_int(), C.c_int(), C.c_double()
+        self._check(self.lib.krr_autotune(self.h, nrhs, reps, C.byref(sp), C.byref(pv), C.byref(ms)))
+        return sp.value, pv.value, ms.value
+
     # ---------------------------------------------------------------- Algorithms 3-5
     def build(self, X, sigma: float, beta: float, k: int, seed: int = 0, anchors=None):
         """Algorithm 5 steps 1-2: anchors (Algorithm 1, or the given ones) and Algorithm 3."""
@@ -375,3 +382,34 @@ def solve(X, y, sigma: float, beta: float, k: int, seed: int = 0, tol: float = 1
     alpha, info = ctx.solve(yd, tol)
     ctx.close()
     return (alpha.cpu() if host else alpha), info
+
+
+def tune_save(path: str):
+    """Write the process-wide tuning table as JSON (krr_tune_save)."""
+    rc = L.load().krr_tune_save(str(path).encode())
+    if rc != 0:
+        raise KRRError(rc, f"cannot write {path}")
+
+
+def tune_load(path: str):
+    """Add the entries of a JSON tuning file to the table (krr_tune_load)."""
+    rc = L.load().krr_tune_load(str(path).encode())
+    if rc != 0:
+        raise KRRError(rc, f"cannot read {path}")
+
+
+def tune_get(key: str):
+    """(splits, pv_form, ms) of one table entry, or None."""
+    sp, pv, ms = C.c_int(), C.c_int(), C.c_double()
+    rc = L.load().krr_tune_get(key.encode(), C.byref(sp), C.byref(pv), C.byref(ms))
+    return None if rc != 0 else (sp.value, pv.value, ms.value)
+
+
+def tune_set(key: str, splits: int, pv: int = 0, ms: float = 0.0):
+    rc = L.load().krr_tune_set(key.encode(), splits, pv, ms)
+    if rc != 0:
+        raise KRRError(rc, "bad tuning entry")
+
+
+def tune_clear():
+    L.load().krr_tune_clear()

@@ -499,7 +499,6 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
         int* h_err = gh.alloc<int>(1);
         // tables: sized for every problem active
         long long nvb_max = 0, nft_max = 0, ntri_max = 0, ngn_max = 0, nred_max = 0, items_max = 0, nvs_max = 0;
-        int kp_max = 0;
         const int chunk_max = nrhs >= 16 ? 16 : nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
         const int vtile = pv_tile_bytes(chunk_max);
         std::vector<int> tcp(nprob, 0);
@@ -511,12 +510,13 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
             ntri_max += c->k_eff;
             ngn_max += (n + GN_ROWS - 1) / GN_ROWS;
             nred_max += (long long)GMAXQ * c->k_eff;
-            tcp[i] = (o.precision == 1 && c->FA) ? 1 : 0;
+            // the grouped tensor-core launch takes K = 64 features (d <= 9); wider problems
+            // built for tensor cores use their own tensor-core product inside the loop
+            tcp[i] = (o.precision == 1 && c->FA && tc_feature_kp(c->d) == 64) ? 1 : 0;
             if (tcp[i]) {
                 const long long ntl = (n + 127) / 128;
-                items_max += ((n + 255) / 256) * std::min<long long>(GSPLIT_CAP, ntl);
+                items_max += ((n + 127) / 128) * std::min<long long>(GSPLIT_CAP, ntl);
                 nvs_max += ((long long)std::max(16, 2 * chunk_max) * ntl * 128 + 255) / 256;
-                kp_max = std::max(kp_max, tc_feature_kp(c->d));
             }
         }
         GVBlk* d_vb = gd.alloc<GVBlk>(nvb_max);
@@ -587,7 +587,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
             // product splits: about four items per SM over all active problems
             long long work = 0;
             for (int i : alist)
-                if (tcp[i]) work += ((probs[i].n + 255) / 256) * ((probs[i].n + 127) / 128);
+                if (tcp[i]) work += ((probs[i].n + 127) / 128) * ((probs[i].n + 127) / 128);
             const long long target = std::max<long long>(4, (work + 4LL * ctx->num_sms - 1) / (4LL * ctx->num_sms));
             int ft = 0, tri = 0, gn = 0, red = 0, it = 0, vs = 0, np = 0;
             any_tc = false;
@@ -606,7 +606,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                 g.splits = 1;
                 g.tc = tcp[i];
                 if (tcp[i]) {
-                    const int ntl = (g.n + 127) / 128, nrb = (g.n + 255) / 256;
+                    const int ntl = (g.n + 127) / 128, nrb = (g.n + 127) / 128;
                     int splits = (int)std::min<long long>(GSPLIT_CAP, std::max<long long>(1, (ntl + target - 1) / target));
                     splits = std::min(splits, ntl);
                     const int tps = (ntl + splits - 1) / splits;
@@ -695,7 +695,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                 const int i = alist[ai];
                 if (tcp[i]) continue;
                 krr_ctx* c = ctxs[i];
-                KRR_RET(square_product(c, pv + off[i], nrhs, qv + off[i], 0));
+                KRR_RET(square_product(c, pv + off[i], nrhs, qv + off[i], (o.precision == 1 && c->FA) ? 1 : 0));
             }
             int c0 = 0, ci = 0;
             while (c0 < nrhs) {
@@ -716,7 +716,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                     PvPrep* ds = d_pp + (size_t)ci * nprob;
                     KRR_TRY_CUDA(cudaMemcpyAsync(ds, hs, sizeof(PvPrep) * np, cudaMemcpyHostToDevice, S));
                     KRR_RET(launch_pv_prep_grouped(ctx, ds, np, n_vs, ch));
-                    KRR_RET(launch_kmvm_tcpv_table(ctx, d_pv, np, items, ch, kp_max, d_err));
+                    KRR_RET(launch_kmvm_tcpv_table(ctx, d_pv, np, items, ch, d_err));
                 }
                 // the reduction (tensor-core problems) or the p . q partials alone (others)
                 const int b0 = colstart[c0], nb = colstart[c0 + ch] - b0;
@@ -981,7 +981,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
             info[i].k_eff = ctxs[i]->k_eff;
             info[i].build_ms = ctxs[i]->build_ms;
             info[i].solve_ms = solve_ms;
-            info[i].product_form = tcp[i] ? 1 : 0;
+            info[i].product_form = (o.precision == 1 && ctxs[i]->FA) ? 1 : 0;
             if (st[i].done) status[i] = KRR_OK;
         }
         cudaStreamSynchronize(S);

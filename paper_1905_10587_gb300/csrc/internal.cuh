@@ -103,6 +103,11 @@ struct krr_ctx {
     double build_ms = 0;
     int rrqr_swaps = 0;        // strong RRQR statistics of the last build
     double rrqr_rho = 0;
+    // ---- work-split tuning (tune.cu): overrides while krr_autotune times candidates
+    bool tuning = false;
+    int force_splits = 0;      // > 0: this column-split count
+    int force_pv = -1;         // >= 0: P.V form of the tensor-core product (1 tensor cores)
+    int last_splits = 0;       // split count of the last product launch
     // device arrays (views into bufs)
     float* P = nullptr;        // n x ps packed points of X
     float* Praw = nullptr;     // n x ps raw coordinates of X (difference form), on demand
@@ -238,6 +243,17 @@ int launch_kmvm_reduce(krr_ctx* ctx, const double* part, int splits, int nr, int
 int launch_kmvm_dsigma(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, long long nc,
                        int d, const float* V, float* Q);
 
+// tune.cu: tuned work splits.  Key of a product configuration; the table entry for it
+// (only with opts.autotune and outside tuning); the split count to use (forced, tuned or
+// the cost model's `analytic`, clamped to [1, ntiles]; also recorded in ctx->last_splits).
+struct TuneEntry {
+    int splits, pv;
+    double ms;
+};
+std::string tune_key(int form, int width, int nrhs, long long n);
+bool tune_lookup(const krr_ctx* ctx, const std::string& key, TuneEntry* out);
+int tuned_splits(krr_ctx* ctx, const std::string& key, int analytic, int ntiles);
+
 // One problem of a (possibly grouped) tensor-core product with P.V on the tensor cores:
 // its features, V tiles, per-column scales, partial sums and work split.  Its items are
 // item0 .. item0 + items - 1 of the launch, item li = (row block li / splits, column
@@ -262,7 +278,7 @@ struct PvPrep {
 int pv_tile_bytes(int nrhs);
 int launch_pv_prep_grouped(krr_ctx* ctx, const PvPrep* tab_dev, int nprob, int nblk, int nrhs);
 int launch_kmvm_tcpv_table(krr_ctx* ctx, const PvProb* table_dev, int nprob, int items, int nrhs,
-                           int kp_max, int* err);
+                           int* err);
 // (K + beta I) V for the built point set in product form 0, 1 or 2 (api.cu)
 int square_product(krr_ctx* ctx, const float* V, int nrhs, float* Q, int form);
 // A replacement whose true residual norm exceeds twice the recursive one restarts the

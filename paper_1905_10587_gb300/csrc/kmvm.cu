@@ -629,8 +629,11 @@ int launch_kmvm(krr_ctx* ctx, const float* Pr, long long nr, const float* Pc, lo
         const int ntiles = (int)ceil_div(nc, KM_BN);
         const int slots = ctx->num_sms * occupancy(ctx, (const void*)fn, KM_THREADS);
         int splits = choose_splits(nblk, ntiles, slots);
+        if (!hp && nr == nc)   // square FP32 products of a built problem: tuned splits
+            splits = tuned_splits(ctx, tune_key(raw ? 2 : 0, dk, chunk, nr), splits, ntiles);
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
+        ctx->last_splits = splits;
         const double ksc = 1.0;   // the exp2 bias correction is applied to the tensor-core form only
         double* part = nullptr;
         if (splits > 1 || hp)

@@ -16,6 +16,7 @@
 #include "internal.cuh"
 
 #include <algorithm>
+#include <string>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -167,6 +168,11 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
         " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T with the types of idesc (kind::f16: FP16 or BF16).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
 }
 // Two floats as one f16x2 word, round to nearest: lo in bits 0-15, hi in bits 16-31.
 __device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
@@ -646,38 +652,36 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
 }
 
 // ------------------------------------------------------------------ multi-RHS product
-// With R right-hand sides the contraction sum_j P_ij V_jq (P_ij = 2^t_ij) is a GEMM
-// of its own and runs as a second tcgen05 MMA chained to the exponent MMA, P held in TMEM:
-//   EXP   S (128 x 64) = FA(128 rows) . FB(64 columns)^T   (the BF16 x3 split above)
-//   split P' = 2^15 2^S = Ph + Pl, both FP16 (22 significant bits), written over S in
-//         place: of every 32 TMEM columns, 16 hold Ph and 16 hold Pl (two K per column)
-//   PV    C (128 x 2R) += Ph . [Vh; Vl]^T + Pl . [Vh; (Vl)]^T  (Pl . Vl unless R = 16)
+// With R right-hand sides the contraction sum_j P_ij V_jq (P_ij = 2^t_ij) is a GEMM of its
+// own and runs as a second tcgen05 MMA, transposed so that its N is the widest possible:
+//   EXP   S (128 rows x 128 columns) = FA(rows) . FB(columns)^T    (the BF16 x3 split above)
+//   split P' = 2^15 2^S = Ph + Pl, both FP16 (22 significant bits), stored to shared memory
+//         as one 256 x 128 K-major operand: rows 0..127 Ph, rows 128..255 Pl
+//   PV    D (M = 128 x N = 256) += [Vh; Vl] . [Ph; Pl]^T over the tile's 128 columns (K)
 // with V'_q = 2^e_q V_q (e_q puts max |V'_q| in [2^14, 2^15)) split V' = Vh + Vl in FP16.
-// Every product of two FP16 values is exact in FP32; the representation errors are
-// about 2^-22 relative per entry (the dropped Pl . Vl term when R = 16 is of that size
-// too).  The scale 2^15 keeps P' in the normal FP16 range down to P = 2^-29.  The V tile
-// has max(16, 2R) rows (Vh of every q, Vl of every q, then zero rows): N is at least 16.  The fold
-// warps read C after every column tile, add its two halves, sum in FP32 over 16 tiles and
-// in FP64 beyond, and write the item's partial sums scaled back by 2^-(15 + e_q).
-// Roles: warp 0 lane 0 copies, warp 1 lane 0 issues MMAs, warps 2..13 are three groups of
-// four that exponentiate every third 128 x 64 unit, warps 14..21 fold C (four per half).
-constexpr int PV_BN = 128;        // columns per column tile
-constexpr int PV_ROWS = 256;      // rows per work item (two 128-row halves)
-constexpr int PV_GROUPS = 3;
-constexpr int PV_THREADS = 32 * (2 + 4 * PV_GROUPS + 8);
-constexpr int PV_UC = 64;          // columns per unit (two units per half per column tile)
-constexpr int PV_NBUF = 6;         // S/P buffers of 64 TMEM columns, two per group
-constexpr int PV_LOOK = 3;         // exponent MMAs issued ahead of the P.V MMAs
-constexpr int PV_FOLD = 16;        // column tiles summed in FP32 before the FP64 fold
-constexpr int PV_NSMAX = 4;        // most column-tile stages
-constexpr uint32_t PV_CCOL = PV_NBUF * PV_UC;   // first C column (4 buffers of 32 after it)
-static_assert(PV_NBUF == 2 * PV_GROUPS && PV_LOOK + PV_GROUPS <= PV_NBUF,
-              "an exponent MMA issued ahead must find its buffer already consumed");
-static_assert(PV_CCOL + 4 * 32 <= 512, "TMEM columns");
+// Row q of D (q < R) and row R + q hold Vh_q and Vl_q against Ph (column i) and Pl (column
+// 128 + i); their four sums are the output for row i.  Every product of two FP16 values is
+// exact in FP32 and the representation errors are about 2^-22 relative per entry; the
+// scale 2^15 keeps P' in the normal FP16 range down to P = 2^-29.
+// Why transposed: a tcgen05.mma costs about 194 cycles whatever its N (measured), so the
+// contraction wants the fewest instructions: one per 16 columns x 128 rows x (hi + lo)
+// here, against two per 16 columns with P as the M = 128 operand.  The A operand is the
+// V tile (2R rows, at least 16); M = 128 reads 128 rows from its address, and the rows
+// past 2R (whatever shared memory follows) only reach D rows that are never read.
+// D accumulates in FP32 over 16 column tiles; warp 0 then folds it into FP64 sums.
+// Roles: warp 0 folds D, warp 1 lane 0 issues MMAs, warps 2..17 exponentiate (tile
+// parity x 64-column half x TMEM lane quarter), warp 18 lane 0 copies.
+constexpr int PV_BN = 128;        // columns per tile
+constexpr int PV_ROWS = 128;      // rows per work item
+constexpr int PV_THREADS = 32 * 19;
+constexpr int PV_NS = 2;          // column-tile stages (features, then V)
+constexpr int PV_FOLD = 16;       // column tiles per FP32 accumulation of D
+constexpr uint32_t PV_PBYTES = 256u * PV_BN * 2u;   // one P operand: 256 rows x 128 FP16
+constexpr uint32_t PV_DCOL = 256;                   // D at TMEM columns 256..511
 
 struct PvShared {
-    uint64_t a_full, a_empty, s_full[PV_NSMAX], s_empty[PV_NSMAX], x_full[PV_NBUF], x_empty[PV_NBUF],
-        p_full[PV_NBUF], c_full[4], c_empty[4], drain;
+    uint64_t a_full, a_empty, f_full[PV_NS], f_empty[PV_NS], v_full[PV_NS], v_empty[PV_NS], t_full[2],
+        t_empty[2], p_full[2], p_empty[2], c_full, c_empty, drain;
     uint32_t tbase;
     int abort;
 };
@@ -693,7 +697,6 @@ struct PvWork {
 struct PvItem {
     const PvProb* pb;
     int rb, sp, t0, t1;
-    uint32_t tileA;
 };
 __device__ __forceinline__ PvItem pv_item(const PvWork& w, int item, int& pc) {
     PvItem it;
@@ -704,42 +707,19 @@ __device__ __forceinline__ PvItem pv_item(const PvWork& w, int item, int& pc) {
         it.pb = &w.one;
     }
     const PvProb& pb = *it.pb;
-    const int li = item - pb.item0;
-    it.rb = li / pb.splits;
-    it.sp = li - it.rb * pb.splits;
+    // split-major: CTAs running at the same time share one column split, whose features
+    // and V tiles then stay in L2 while every row block streams them
+    const int li = item - pb.item0, nrb = pb.items / pb.splits;
+    it.sp = li / nrb;
+    it.rb = li - it.sp * nrb;
     it.t0 = it.sp * pb.tps;
     it.t1 = min(it.t0 + pb.tps, (pb.nc + PV_BN - 1) / PV_BN);
-    it.tileA = 128u * (uint32_t)pb.Kp * 2u;
     return it;
 }
-
-// Walks the (item, column tile, unit) sequence of one CTA; U counts units, T tiles and
-// ic items, in the same order for every role.
-struct PvCursor {
-    PvItem it;
-    int item, t, u, pc;
-    uint32_t U, T, ic;
-    bool valid;
-    __device__ void set_item(const PvWork& w, int i, int items) {
-        item = i;
-        valid = i < items;
-        if (valid) {
-            it = pv_item(w, i, pc);
-            t = it.t0;
-        }
-    }
-    __device__ void advance(const PvWork& w, int items) {
-        ++U;
-        if (++u == 4) {
-            u = 0;
-            ++T;
-            if (++t == it.t1) {
-                ++ic;
-                set_item(w, item + (int)gridDim.x, items);
-            }
-        }
-    }
-};
+// the item's D folds end at its local tiles FOLD - 1, 2 FOLD - 1, ... and at its last tile
+__device__ __forceinline__ bool pv_fold_end(int t, const PvItem& it) {
+    return t == it.t1 - 1 || ((t - it.t0) % PV_FOLD) == PV_FOLD - 1;
+}
 
 // 2^15 2^t for two neighbouring columns, as FP16 pairs hi (Ph) and lo (Pl = P' - Ph rounded)
 __device__ __forceinline__ void pv_split2(uint32_t t0, uint32_t t1, uint32_t& hi, uint32_t& lo) {
@@ -755,41 +735,45 @@ __device__ __forceinline__ void pv_split2(uint32_t t0, uint32_t t1, uint32_t& hi
     lo = pack_f16x2(r0, r1);
 }
 
-// stage = bytes of one column-tile stage (features of the widest problem, then V), abytes =
-// bytes of the row operand region (two tiles of the widest problem).
+// Feature tiles have K = Kp = 64 (d <= 9) for every problem of the launch.
 template <int NRHS>
 __global__ void __launch_bounds__(PV_THREADS, 1)
-k_kmvm_tcpv(const __grid_constant__ PvWork w, int items, int ns, uint32_t stage, uint32_t abytes,
-            int* __restrict__ err, long long wlimit, int stall_copies) {
+k_kmvm_tcpv(const __grid_constant__ PvWork w, int items, int* __restrict__ err, long long wlimit,
+            int stall_copies) {
     static_assert(NRHS == 1 || NRHS == 2 || NRHS == 4 || NRHS == 8 || NRHS == 16, "right-hand sides");
     constexpr uint32_t VROWS = 2 * NRHS < 16 ? 16 : 2 * NRHS;   // Vh rows, Vl rows, zero rows
     constexpr uint32_t VSLAB = VROWS * 128u;          // bytes of 64 K of the V tile
     constexpr uint32_t VBYTES = 2 * VSLAB;            // one 128-column V tile
+    constexpr int Kp = 64;
+    constexpr uint32_t tileA = 128u * Kp * 2u;        // a 128-row feature tile
+    constexpr uint32_t stage = tileA + VBYTES;        // column features, then V
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const uint32_t vstage = stage - VBYTES;           // offset of V inside a stage
-    unsigned char* sA = smem;                         // 256 rows
-    unsigned char* sB = smem + abytes;                // ns stages: column features, then V
-    double* sAcc = reinterpret_cast<double*>(sB + (size_t)ns * stage);   // [NRHS][256] FP64 sums
-    PvShared* sh = reinterpret_cast<PvShared*>(sAcc + NRHS * 256);
+    unsigned char* sA = smem;                                   // the item's 128 rows
+    unsigned char* sB = sA + tileA;                             // PV_NS stages
+    unsigned char* sP = sB + PV_NS * stage;                     // 2 P operands
+    double* sAcc = reinterpret_cast<double*>(sP + 2 * PV_PBYTES);      // [NRHS][128] FP64
+    float* sFold = reinterpret_cast<float*>(sAcc + NRHS * PV_ROWS);    // [NRHS][128] one fold
+    PvShared* sh = reinterpret_cast<PvShared*>(sFold + NRHS * PV_ROWS);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         mbar_init(&sh->a_full, 1);
         mbar_init(&sh->a_empty, 1);
-        for (int s = 0; s < PV_NSMAX; ++s) {
-            mbar_init(&sh->s_full[s], 1);
-            mbar_init(&sh->s_empty[s], 1);
+        for (int s = 0; s < PV_NS; ++s) {
+            mbar_init(&sh->f_full[s], 1);
+            mbar_init(&sh->f_empty[s], 1);
+            mbar_init(&sh->v_full[s], 1);
+            mbar_init(&sh->v_empty[s], 1);
         }
-        for (int b = 0; b < PV_NBUF; ++b) {
-            mbar_init(&sh->x_full[b], 1);
-            mbar_init(&sh->x_empty[b], 1);
-            mbar_init(&sh->p_full[b], 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->t_full[b], 1);
+            mbar_init(&sh->t_empty[b], 8);     // the 8 exponent warps of the tile's parity
+            mbar_init(&sh->p_full[b], 8);
+            mbar_init(&sh->p_empty[b], 1);
         }
-        for (int c = 0; c < 4; ++c) {
-            mbar_init(&sh->c_full[c], 1);
-            mbar_init(&sh->c_empty[c], 4);
-        }
+        mbar_init(&sh->c_full, 1);
+        mbar_init(&sh->c_empty, 1);
         mbar_init(&sh->drain, 1);
         sh->abort = 0;
         fence_mbar_init();
@@ -806,101 +790,116 @@ k_kmvm_tcpv(const __grid_constant__ PvWork w, int items, int ns, uint32_t stage,
         atomicExch(err, 1);
     };
 
-    if (warp == 0) {
+    if (warp == 18) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             uint32_t T = 0, ic = 0;
             int pc = 0;
             for (int item = blockIdx.x; item < items && !*abort && !stall_copies; item += gridDim.x) {
                 const PvItem it = pv_item(w, item, pc);
-                const uint32_t tileA = it.tileA;
                 if (!mbar_wait(&sh->a_empty, (ic & 1u) ^ 1u, wlimit)) { give_up(); break; }
-                mbar_expect_tx(&sh->a_full, 2 * tileA);
-                bulk_g2s(sA, it.pb->FA + (size_t)it.rb * 2 * tileA, 2 * tileA, &sh->a_full);
+                mbar_expect_tx(&sh->a_full, tileA);
+                bulk_g2s(sA, it.pb->FA + (size_t)it.rb * tileA, tileA, &sh->a_full);
                 ++ic;
                 bool ok = true;
-                for (int t = it.t0; t < it.t1; ++t) {
-                    const int s = (int)(T % (uint32_t)ns);
-                    if (!mbar_wait(&sh->s_empty[s], ((T / ns) & 1u) ^ 1u, wlimit)) { ok = false; break; }
-                    mbar_expect_tx(&sh->s_full[s], tileA + VBYTES);
-                    bulk_g2s(sB + (size_t)s * stage, it.pb->FB + (size_t)t * tileA, tileA, &sh->s_full[s]);
-                    bulk_g2s(sB + (size_t)s * stage + vstage, it.pb->Vt + (size_t)t * VBYTES, VBYTES,
-                             &sh->s_full[s]);
-                    ++T;
+                // features are released by the exponent MMA and V by the P.V MMA, which
+                // runs a tile later: the next features start loading that much earlier
+                for (int t = it.t0; t < it.t1; ++t, ++T) {
+                    const int s = (int)(T % PV_NS);
+                    const uint32_t ph = ((T / PV_NS) & 1u) ^ 1u;
+                    if (!mbar_wait(&sh->f_empty[s], ph, wlimit)) { ok = false; break; }
+                    mbar_expect_tx(&sh->f_full[s], tileA);
+                    bulk_g2s(sB + s * stage, it.pb->FB + (size_t)t * tileA, tileA, &sh->f_full[s]);
+                    if (!mbar_wait(&sh->v_empty[s], ph, wlimit)) {
+                        mbar_wait(&sh->f_full[s], (T / PV_NS) & 1u, wlimit);   // the copy just issued
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&sh->v_full[s], VBYTES);
+                    bulk_g2s(sB + s * stage + tileA, it.pb->Vt + (size_t)t * VBYTES, VBYTES, &sh->v_full[s]);
                 }
                 if (!ok) { give_up(); break; }
             }
             // drain: one arrival per barrier phase, so a parity wait on the newest is exact
-            for (uint32_t i = 0; i < (T < (uint32_t)ns ? T : (uint32_t)ns); ++i) {
+            // (a tile whose V copy was never issued has its features' copy waited on)
+            for (uint32_t i = 0; i < (T < (uint32_t)PV_NS ? T : (uint32_t)PV_NS); ++i) {
                 const uint32_t gg = T - 1 - i;
-                mbar_wait(&sh->s_full[gg % ns], (gg / ns) & 1u, wlimit);
+                mbar_wait(&sh->f_full[gg % PV_NS], (gg / PV_NS) & 1u, wlimit);
+                mbar_wait(&sh->v_full[gg % PV_NS], (gg / PV_NS) & 1u, wlimit);
             }
             if (ic > 0) mbar_wait(&sh->a_full, (ic - 1) & 1u, wlimit);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id_exp = idesc_bf16(128, PV_UC);
-            const uint32_t id_hi = idesc_f16(128, VROWS), id_lo = idesc_f16(128, 16);
-            PvCursor e{}, p{};
-            e.set_item(w, blockIdx.x, items);
-            p.set_item(w, blockIdx.x, items);
+            const uint32_t id_exp = idesc_bf16(128, PV_BN), id_pv = idesc_f16(128, 256);
             bool issued = false, ok = true;
-            auto exp_mma = [&](const PvCursor& c) -> bool {
-                if (c.u == 0 && c.t == c.it.t0 && !mbar_wait(&sh->a_full, c.ic & 1u, wlimit)) return false;
-                const int s = (int)(c.T % (uint32_t)ns);
-                if (c.u == 0 && !mbar_wait(&sh->s_full[s], (c.T / ns) & 1u, wlimit)) return false;
-                const int b = (int)(c.U % PV_NBUF);
-                if (!mbar_wait(&sh->x_empty[b], ((c.U / PV_NBUF) & 1u) ^ 1u, wlimit)) return false;
-                tc_fence_after();
-                const int h = c.u >> 1, cc = c.u & 1;
-                const uint32_t a_addr = smem_u32(sA) + (uint32_t)h * c.it.tileA;
-                // columns 64 cc .. 64 cc + 63 of the tile: rows 64 cc.. of every K slab
-                const uint32_t b_addr = smem_u32(sB + (size_t)s * stage) + (uint32_t)cc * 8192u;
-                for (int kk = 0; kk < c.it.pb->Kp / 16; ++kk) {
-                    const uint32_t koff = (uint32_t)(kk >> 2) * 16384u + (uint32_t)(kk & 3) * 32u;
-                    mma_bf16(tmem + (uint32_t)(b * PV_UC), smem_desc_sw128(a_addr + koff),
-                             smem_desc_sw128(b_addr + koff), id_exp, kk > 0 ? 1u : 0u);
-                }
-                mma_commit(&sh->x_full[b]);
-                if (c.u == 3 && c.t == c.it.t1 - 1) mma_commit(&sh->a_empty);   // last use of the rows
-                issued = true;
-                return true;
-            };
-            auto pv_mma = [&](const PvCursor& c) -> bool {
-                const int b = (int)(c.U % PV_NBUF);
-                if (!mbar_wait(&sh->p_full[b], (c.U / PV_NBUF) & 1u, wlimit)) return false;
-                const int h = c.u >> 1, cc = c.u & 1;
-                const int ci = 2 * h + (int)(c.T & 1u);
-                if (cc == 0 && !mbar_wait(&sh->c_empty[ci], ((c.T >> 1) & 1u) ^ 1u, wlimit)) return false;
-                tc_fence_after();
-                const int s = (int)(c.T % (uint32_t)ns);
-                const uint32_t v_addr = smem_u32(sB + (size_t)s * stage + vstage) + (uint32_t)cc * VSLAB;
-                const uint32_t d = tmem + PV_CCOL + 32u * ci;
-                const uint32_t pb = tmem + (uint32_t)(b * PV_UC);
-                for (int kk = 0; kk < PV_UC / 16; ++kk) {
-                    const uint32_t a_hi = pb + 32u * (kk >> 1) + 8u * (kk & 1);
-                    const uint64_t bd = smem_desc_sw128(v_addr + 32u * kk);
-                    mma_f16_ts(d, a_hi, bd, id_hi, (cc > 0 || kk > 0) ? 1u : 0u);
-                    mma_f16_ts(d, a_hi + 16u, bd, id_lo, 1u);
-                }
-                mma_commit(&sh->x_empty[b]);
-                if (cc == 1) mma_commit(&sh->c_full[ci]);
-                if (c.u == 3) mma_commit(&sh->s_empty[s]);
-                return true;
-            };
-            for (int i = 0; i < PV_LOOK && e.valid && ok; ++i) {
-                ok = exp_mma(e);
-                e.advance(w, items);
+            // EXP of tile T + 1 is issued before PV of tile T, so that the exponentials of the
+            // next tile run while the tensor core contracts the current one
+            int pc_e = 0, item_e = blockIdx.x, t_e = 0;
+            uint32_t T_e = 0, ic_e = 0;
+            PvItem it_e{};
+            bool have_e = item_e < items;
+            if (have_e) {
+                it_e = pv_item(w, item_e, pc_e);
+                t_e = it_e.t0;
             }
-            while (ok && p.valid && !*abort) {
-                if (e.valid) {
-                    ok = exp_mma(e);
-                    e.advance(w, items);
-                    if (!ok) break;
+            auto exp_next = [&]() -> bool {      // EXP of the next tile in sequence, then advance
+                const int s = (int)(T_e % PV_NS), b = (int)(T_e & 1u);
+                if (t_e == it_e.t0 && !mbar_wait(&sh->a_full, ic_e & 1u, wlimit)) return false;
+                if (!mbar_wait(&sh->f_full[s], (T_e / PV_NS) & 1u, wlimit)) return false;
+                if (!mbar_wait(&sh->t_empty[b], ((T_e >> 1) & 1u) ^ 1u, wlimit)) return false;
+                tc_fence_after();
+                const uint32_t a_addr = smem_u32(sA), b_addr = smem_u32(sB + s * stage);
+                for (int kk = 0; kk < Kp / 16; ++kk)
+                    mma_bf16(tmem + (uint32_t)(b * PV_BN), smem_desc_sw128(a_addr + (uint32_t)kk * 32u),
+                             smem_desc_sw128(b_addr + (uint32_t)kk * 32u), id_exp, kk > 0 ? 1u : 0u);
+                mma_commit(&sh->t_full[b]);
+                mma_commit(&sh->f_empty[s]);         // the features of this stage are used up
+                issued = true;
+                ++T_e;
+                if (++t_e == it_e.t1) {
+                    mma_commit(&sh->a_empty);    // the last use of the item's rows
+                    ++ic_e;
+                    item_e += gridDim.x;
+                    have_e = item_e < items;
+                    if (have_e) {
+                        it_e = pv_item(w, item_e, pc_e);
+                        t_e = it_e.t0;
+                    }
                 }
-                ok = pv_mma(p);
-                p.advance(w, items);
+                return true;
+            };
+            if (have_e) ok = exp_next();
+            uint32_t T = 0, fc = 0;
+            int pc = 0;
+            for (int item = blockIdx.x; item < items && ok && !*abort; item += gridDim.x) {
+                const PvItem it = pv_item(w, item, pc);
+                bool fold_start = true;
+                for (int t = it.t0; t < it.t1; ++t, ++T) {
+                    if (have_e && !(ok = exp_next())) break;
+                    const int s = (int)(T % PV_NS), pb = (int)(T & 1u);
+                    if (!(ok = mbar_wait(&sh->p_full[pb], (T >> 1) & 1u, wlimit))) break;
+                    if (!(ok = mbar_wait(&sh->v_full[s], (T / PV_NS) & 1u, wlimit))) break;
+                    if (fold_start && !(ok = mbar_wait(&sh->c_empty, (fc & 1u) ^ 1u, wlimit))) break;
+                    tc_fence_after();
+                    const uint32_t v_addr = smem_u32(sB + s * stage + tileA);
+                    const uint32_t p_addr = smem_u32(sP + pb * PV_PBYTES);
+                    for (int kk = 0; kk < PV_BN / 16; ++kk) {
+                        const uint32_t ko = (uint32_t)(kk >> 2), ki = (uint32_t)(kk & 3) * 32u;
+                        mma_f16(tmem + PV_DCOL, smem_desc_sw128(v_addr + ko * VSLAB + ki),
+                                smem_desc_sw128(p_addr + ko * 32768u + ki), id_pv,
+                                (fold_start && kk == 0) ? 0u : 1u);
+                    }
+                    fold_start = false;
+                    mma_commit(&sh->p_empty[pb]);
+                    mma_commit(&sh->v_empty[s]);
+                    if (pv_fold_end(t, it)) {
+                        mma_commit(&sh->c_full);
+                        ++fc;
+                        fold_start = true;
+                    }
+                }
             }
             if (!ok) give_up();
             if (issued) {   // every MMA issued has finished once the drain phase completes
@@ -908,97 +907,106 @@ k_kmvm_tcpv(const __grid_constant__ PvWork w, int items, int ns, uint32_t stage,
                 mbar_wait(&sh->drain, 0, wlimit);
             }
         }
-    } else if (warp < 2 + 4 * PV_GROUPS) {
+    } else if (warp >= 2) {
         // ---------------------------------------------------------- exponentials
-        const int grp = (warp - 2) >> 2, quarter = warp & 3;
-        uint32_t total = 0;
-        int pc = 0;
-        for (int item = blockIdx.x; item < items; item += gridDim.x) {
-            const PvItem it = pv_item(w, item, pc);
-            total += 4u * (uint32_t)(it.t1 - it.t0);
-        }
-        for (uint32_t U = grp; U < total && !*abort; U += PV_GROUPS) {
-            const int b = (int)(U % PV_NBUF);
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&sh->x_full[b], (U / PV_NBUF) & 1u, wlimit));
-            if (!ok) { if (lane == 0) give_up(); break; }
-            tc_fence_after();
-            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * PV_UC);
-#pragma unroll 1
-            for (int c32 = 0; c32 < PV_UC / 32; ++c32) {
-                uint32_t r[32], o[32];
-                tmem_ld32(tb + 32u * c32, r);
-                tmem_wait_ld(r);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) pv_split2(r[2 * j], r[2 * j + 1], o[j], o[16 + j]);
-                tmem_st32(tb + 32u * c32, o);
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh->p_full[b]);
-        }
-    } else {
-        // ---------------------------------------------------------- fold
-        const int f = warp - 2 - 4 * PV_GROUPS;       // 0..7
-        const int h = f >> 2, quarter = warp & 3;
-        const int lrow = h * 128 + quarter * 32 + lane;
+        // warp e (0..15): TMEM lanes of its quarter (rows quarter*32 .. +31), the 64-column
+        // half chalf of every tile of parity par; P goes to the tile's P operand, row i
+        // (Ph) and row 128 + i (Pl), K-major with the 128-byte swizzle (slab = chalf)
+        const int e = warp - 2, quarter = warp & 3, chalf = (e >> 2) & 1, par = e >> 3;
+        const int i = quarter * 32 + lane;
         uint32_t T = 0;
         int pc = 0;
         for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
             const PvItem it = pv_item(w, item, pc);
-            const int t0 = it.t0, t1 = it.t1;
-            float acc[NRHS];
-#pragma unroll
-            for (int q = 0; q < NRHS; ++q) {
-                acc[q] = 0.f;
-                sAcc[q * 256 + lrow] = 0.0;
-            }
             bool ok = true;
-            int nf = 0;
-            for (int t = t0; t < t1; ++t, ++T) {
-                const int ci = 2 * h + (int)(T & 1u);
-                ok = __all_sync(0xffffffffu, mbar_wait(&sh->c_full[ci], (T >> 1) & 1u, wlimit));
+            for (int t = it.t0; t < it.t1; ++t, ++T) {
+                if ((int)(T & 1u) != par) continue;
+                const int b = par;
+                ok = mbar_wait(&sh->t_full[b], (T >> 1) & 1u, wlimit) &&
+                     mbar_wait(&sh->p_empty[b], ((T >> 1) & 1u) ^ 1u, wlimit);
+                ok = __all_sync(0xffffffffu, ok);
                 if (!ok) { if (lane == 0) give_up(); break; }
                 tc_fence_after();
-                const uint32_t ca = tmem + ((uint32_t)(quarter * 32) << 16) + PV_CCOL + 32u * ci;
-                if constexpr (NRHS == 16) {
-                    uint32_t c[32];
-                    tmem_ld32(ca, c);
-                    tmem_wait_ld(c);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->c_empty[ci]);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[q] += __uint_as_float(c[q]) + __uint_as_float(c[16 + q]);
-                } else {
-                    uint32_t c[16];
-                    tmem_ld16(ca, c);
-                    tmem_wait_ld16(c);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->c_empty[ci]);
-#pragma unroll
-                    for (int q = 0; q < NRHS; ++q)
-                        acc[q] += __uint_as_float(c[q]) + __uint_as_float(c[NRHS + q]);
-                }
-                if (++nf == PV_FOLD || t == t1 - 1) {
-#pragma unroll
-                    for (int q = 0; q < NRHS; ++q) {
-                        sAcc[q * 256 + lrow] += (double)acc[q];
-                        acc[q] = 0.f;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * PV_BN + chalf * 64);
+                unsigned char* ps = sP + b * PV_PBYTES + chalf * 32768u;   // slab chalf
+#pragma unroll 1
+                for (int c32 = 0; c32 < 2; ++c32) {
+                    uint32_t r[32], hi[16], lo[16];
+                    tmem_ld32(tb + 32u * c32, r);
+                    tmem_wait_ld(r);
+                    if (c32 == 1) {                 // S of this tile fully read
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh->t_empty[b]);
                     }
-                    nf = 0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) pv_split2(r[2 * j], r[2 * j + 1], hi[j], lo[j]);
+                    // columns 32 c32 .. +31 of the slab: 16-byte chunks 4 c32 .. 4 c32 + 3
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const uint32_t kc = (uint32_t)(4 * c32 + m);
+                        const uint32_t oh = (uint32_t)i * 128u + ((kc ^ (uint32_t)(i & 7)) << 4);
+                        const uint32_t ol = (uint32_t)(128 + i) * 128u + ((kc ^ (uint32_t)(i & 7)) << 4);
+                        *reinterpret_cast<uint4*>(ps + oh) = make_uint4(hi[4 * m], hi[4 * m + 1], hi[4 * m + 2], hi[4 * m + 3]);
+                        *reinterpret_cast<uint4*>(ps + ol) = make_uint4(lo[4 * m], lo[4 * m + 1], lo[4 * m + 2], lo[4 * m + 3]);
+                    }
                 }
+                fence_proxy_async();                // the stores, visible to the MMA's reads
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->p_full[b]);
             }
             if (!ok) break;
-            const long long row = (long long)it.rb * PV_ROWS + lrow;
-            const int nr = it.pb->nr;
-            if (row < nr) {
-                double* part = it.pb->part;
-                const double* vsc = it.pb->vsc;
+        }
+    } else {
+        // ---------------------------------------------------------- fold (warp 0)
+        // D lanes 0..31 are V rows: lane q < NRHS is Vh_q, lane NRHS + q is Vl_q; columns
+        // 0..127 meet Ph (row i), 128..255 meet Pl (row i).  One fold: every lane sums its
+        // Ph and Pl columns, lane q adds lane NRHS + q, and the FP32 fold goes to sFold;
+        // after c_empty the fold is added into the FP64 sums.
+        uint32_t fc = 0;
+        int pc = 0;
+        for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
+            const PvItem it = pv_item(w, item, pc);
+            for (int e = lane; e < NRHS * PV_ROWS; e += 32) sAcc[e] = 0.0;
+            bool ok = true;
+            for (int t = it.t0; t < it.t1; ++t) {
+                if (!pv_fold_end(t, it)) continue;
+                ok = __all_sync(0xffffffffu, mbar_wait(&sh->c_full, fc & 1u, wlimit));
+                if (!ok) { if (lane == 0) give_up(); break; }
+                ++fc;
+                tc_fence_after();
+#pragma unroll 1
+                for (int c = 0; c < PV_ROWS / 32; ++c) {
+                    uint32_t dh[32], dl[32];
+                    tmem_ld32(tmem + PV_DCOL + 32u * c, dh);
+                    tmem_ld32(tmem + PV_DCOL + 128u + 32u * c, dl);
+                    tmem_wait_ld(dh);
+                    tmem_wait_ld(dl);
 #pragma unroll
-                for (int q = 0; q < NRHS; ++q)
-                    part[((size_t)it.sp * NRHS + q) * nr + row] = sAcc[q * 256 + lrow] * vsc[q];
+                    for (int j = 0; j < 32; ++j) {
+                        float v = __uint_as_float(dh[j]) + __uint_as_float(dl[j]);
+                        v += __shfl_down_sync(0xffffffffu, v, NRHS);
+                        if (lane < NRHS) sFold[lane * PV_ROWS + 32 * c + j] = v;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->c_empty);
+                for (int e = lane; e < NRHS * PV_ROWS; e += 32) sAcc[e] += (double)sFold[e];
+                __syncwarp();
             }
+            if (!ok) break;
+            const int nr = it.pb->nr;
+            double* part = it.pb->part;
+            const double* vsc = it.pb->vsc;
+            for (int q = 0; q < NRHS; ++q) {
+                const double sc = vsc[q];
+                for (int r = lane; r < PV_ROWS; r += 32) {
+                    const long long row = (long long)it.rb * PV_ROWS + r;
+                    if (row < nr) part[((size_t)it.sp * NRHS + q) * nr + row] = sAcc[q * PV_ROWS + r] * sc;
+                }
+            }
+            __syncwarp();
         }
     }
     __syncwarp();
@@ -1366,19 +1374,18 @@ int launch_pv_prep_grouped(krr_ctx* ctx, const PvPrep* tab_dev, int nprob, int n
     return KRR_OK;
 }
 
-// One launch of the product over the items of every problem in the device table (item0
-// prefix, `items` in all); kp_max is the widest feature row of any of them.
-int launch_kmvm_tcpv_table(krr_ctx* ctx, const PvProb* table_dev, int nprob, int items, int nrhs,
-                           int kp_max, int* err) {
+// Shared memory of the P.V kernel for nrhs right-hand sides (K = 64 features).
+static size_t pv_smem_bytes(int nrhs) {
+    const size_t tileA = 128u * 64u * 2u;
     const size_t vbytes = (size_t)pv_tile_bytes(nrhs);
-    const uint32_t tileA = 128u * kp_max * 2u;
-    int optin = 0;
-    KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    const size_t fixed = 2 * (size_t)tileA + (size_t)256 * nrhs * 8 + sizeof(PvShared) + 1024;
-    const size_t stage = tileA + vbytes;
-    const int ns = (int)std::min<size_t>(PV_NSMAX, (size_t)optin > fixed ? ((size_t)optin - fixed) / stage : 0);
-    if (ns < 2) return fail(ctx, KRR_E_INVAL, "tensor-core product: features too wide for the P.V form");
-    const size_t smem_launch = std::max<size_t>(fixed + ns * stage, 120 * 1024);
+    return 1024 + tileA + PV_NS * (tileA + vbytes) + 2 * (size_t)PV_PBYTES + (size_t)nrhs * PV_ROWS * 12 +
+           sizeof(PvShared);
+}
+
+// One launch of the product over the items of every problem in the device table (item0
+// prefix, `items` in all); every problem has K = 64 features (d <= 9).
+int launch_kmvm_tcpv_table(krr_ctx* ctx, const PvProb* table_dev, int nprob, int items, int nrhs,
+                           int* err) {
     auto fn = nrhs == 16 ? &k_kmvm_tcpv<16> : nrhs == 8 ? &k_kmvm_tcpv<8> : nrhs == 4 ? &k_kmvm_tcpv<4>
             : nrhs == 2 ? &k_kmvm_tcpv<2> : &k_kmvm_tcpv<1>;
     KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
@@ -1388,8 +1395,7 @@ int launch_kmvm_tcpv_table(krr_ctx* ctx, const PvProb* table_dev, int nprob, int
     w.table = table_dev;
     w.nprob = nprob;
     const int grid = std::min(items, ctx->num_sms);
-    fn<<<grid, PV_THREADS, smem_launch, ctx->stream>>>(w, items, ns, (uint32_t)stage, 2u * tileA, err, wlimit,
-                                                       ctx->opts.test_stall_copies);
+    fn<<<grid, PV_THREADS, pv_smem_bytes(nrhs), ctx->stream>>>(w, items, err, wlimit, ctx->opts.test_stall_copies);
     KRR_CHECK_LAUNCH();
     return KRR_OK;
 }
@@ -1411,24 +1417,19 @@ static int launch_kmvm_tcpv(krr_ctx* ctx, const unsigned char* FA, long long nr,
     const long long nsplit = (long long)vrows * ncp;
     k_pv_vsplit<<<ceil_div(nsplit, 256), 256, 0, ctx->stream>>>(V, (int)nc, (int)nc, ncp, nrhs, vrows, vexp, Vt);
     KRR_CHECK_LAUNCH();
-    const uint32_t tileA = 128u * Kp * 2u;
-    const size_t fixed = 2 * (size_t)tileA + (size_t)256 * nrhs * 8 + sizeof(PvShared) + 1024;
-    const size_t stage = tileA + vbytes;
-    int optin = 0;
-    KRR_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    const size_t cap = (size_t)optin;
-    const int ns = (int)std::min<size_t>(PV_NSMAX, cap > fixed ? (cap - fixed) / stage : 0);
-    if (ns < 2) return fail(ctx, KRR_E_INVAL, "tensor-core product: features too wide for the P.V form");
-    const size_t smem = fixed + ns * stage;
-    const size_t smem_launch = std::max<size_t>(smem, 120 * 1024);   // one CTA per SM (TMEM)
+    if (Kp != 64) return fail(ctx, KRR_E_INVAL, "P.V on tensor cores needs d <= 9");
     auto fn = nrhs == 16 ? &k_kmvm_tcpv<16> : nrhs == 8 ? &k_kmvm_tcpv<8> : nrhs == 4 ? &k_kmvm_tcpv<4>
             : nrhs == 2 ? &k_kmvm_tcpv<2> : &k_kmvm_tcpv<1>;
     KRR_RET(allow_max_dynamic_smem(ctx, (const void*)fn));
     const int nrb = (int)ceil_div(nr, PV_ROWS);
     const int ntiles = ncp / PV_BN;
-    int splits = 1;
+    // items run split-major: one split's features and V tiles (all row blocks stream them
+    // at about the same time) should fit in about a third of the 129 MB L2
+    const long long col_bytes = (long long)ntiles * (128 * 64 * 2 + (long long)pv_tile_bytes(nrhs));
+    const int sc_min = (int)std::min<long long>(std::max<long long>(1, ntiles), ceil_div(col_bytes, 40LL << 20));
+    int splits = sc_min;
     long long best = -1;
-    for (int sc = 1; sc <= std::min(64, ntiles); ++sc) {   // as in launch_kmvm_tc
+    for (int sc = sc_min; sc <= std::max(sc_min, std::min(64, ntiles)); ++sc) {   // as in launch_kmvm_tc
         const long long per = (ntiles + sc - 1) / sc;
         const long long waves = ((long long)nrb * sc + ctx->num_sms - 1) / ctx->num_sms;
         const long long cost = waves * (per + 8);
@@ -1437,8 +1438,10 @@ static int launch_kmvm_tcpv(krr_ctx* ctx, const unsigned char* FA, long long nr,
             splits = sc;
         }
     }
+    splits = std::max(sc_min, tuned_splits(ctx, tune_key(1, Kp, nrhs, nr), splits, ntiles));
     const int tps = (ntiles + splits - 1) / splits;
     splits = (ntiles + tps - 1) / tps;
+    ctx->last_splits = splits;
     const int items = nrb * splits;
     double* part;
     KRR_RET(bufT(ctx, "tc_part", (size_t)splits * nrhs * nr, &part));
@@ -1449,8 +1452,7 @@ static int launch_kmvm_tcpv(krr_ctx* ctx, const unsigned char* FA, long long nr,
     w.table = nullptr;
     w.nprob = 1;
     w.one = PvProb{FA, FB, Vt, vsc, part, (int)nr, (int)nc, Kp, splits, tps, items, 0, 0};
-    fn<<<grid, PV_THREADS, smem_launch, ctx->stream>>>(w, items, ns, (uint32_t)stage, 2u * tileA, err, wlimit,
-                                                       ctx->opts.test_stall_copies);
+    fn<<<grid, PV_THREADS, pv_smem_bytes(nrhs), ctx->stream>>>(w, items, err, wlimit, ctx->opts.test_stall_copies);
     KRR_CHECK_LAUNCH();
     return launch_kmvm_reduce(ctx, part, splits, (int)nr, nrhs, V, (int)nc, beta, Q, (int)nr);
 }
@@ -1476,7 +1478,14 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
     while (done < nrhs) {
         const int left = nrhs - done;
         const int chunk = left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        if (!hp && (ctx->opts.tc_pv == 2 || (ctx->opts.tc_pv == 1 && chunk >= 8))) {
+        const std::string key = tune_key(1, Kp, chunk, nr);
+        bool use_pv = !hp && Kp == 64 && (ctx->opts.tc_pv == 2 || (ctx->opts.tc_pv == 1 && chunk >= 8));
+        TuneEntry te;
+        if (!hp && Kp == 64) {
+            if (ctx->force_pv >= 0) use_pv = ctx->force_pv == 1;
+            else if (ctx->opts.tc_pv != 0 && tune_lookup(ctx, key, &te)) use_pv = te.pv == 1;
+        }
+        if (use_pv) {
             KRR_RET(launch_kmvm_tcpv(ctx, FA, nr, FB, nc, Kp, beta, V + (size_t)done * nc, chunk,
                                      Q + (size_t)done * nr, err));
             done += chunk;
@@ -1515,8 +1524,10 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
                 splits = sc;
             }
         }
+        splits = tuned_splits(ctx, key, splits, ntiles);
         const int tps = (ntiles + splits - 1) / splits;
         splits = (ntiles + tps - 1) / tps;
+        ctx->last_splits = splits;
         const int items = nrb * splits;
         double* part;
         KRR_RET(bufT(ctx, "tc_part", (size_t)4 * splits * chunk * nr, &part));
