@@ -319,7 +319,31 @@ def run_gpu(args):
     p = _workload(args.n, rank)
     X = torch.from_numpy(p.X).to(dev)
     Y = torch.from_numpy(p.Y).to(dev)
-    ctx = api.KRR(precision=args.precision)
+    # work-split tuning (outside the timed region): the table file from an earlier run if
+    # there is one, else the product of the built problem timed for every candidate split
+    tune = None
+    if not args.no_autotune:
+        if os.path.exists(args.tune_file):
+            try:
+                api.tune_load(args.tune_file)
+            except api.KRRError:
+                pass
+        tctx = api.KRR(precision=args.precision)
+        tctx.build(X, p.sigma, p.beta, p.k, seed=1)
+        width = 64 if args.precision == 1 else p.X.shape[1]
+        key = f"form={args.precision} w={width} r=1 lg={int(np.floor(np.log2(p.n)))}"
+        got = api.tune_get(key)
+        if got is None:
+            tctx.autotune(nrhs=1, reps=3)
+            got = api.tune_get(key)
+        tctx.close()
+        tune = {"key": key, "splits": got[0], "pv": got[1], "ms_when_tuned": got[2], "file": args.tune_file}
+        if rank == 0:
+            try:
+                api.tune_save(args.tune_file)
+            except api.KRRError:
+                pass
+    ctx = api.KRR(precision=args.precision, autotune=0 if args.no_autotune else 1)
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
 
     def step():
@@ -378,7 +402,7 @@ def run_gpu(args):
                           "precision": ("tensor-core BF16x3 exponent tiles (tcgen05), FP32 accumulation"
                                         if args.precision == 1 else "FP32 kernel tiles")
                           + "; FP64 CG scalars; float-float residual replacement",
-                          "replicas": world},
+                          "replicas": world, "work_split": tune if tune else "cost model"},
                "roofline": roof, "clocks": clocks, "gpu_launches": launches,
                "mvm_pairs_per_s": pairs * kcnt / (kms / 1e3) if kcnt else None,
                "solve": {"iters": last["iters"], "sweeps": last["sweeps"], "k_eff": last["k_eff"],
@@ -713,6 +737,35 @@ def run_condition(args):
     return 0
 
 
+def run_product(args):
+    """Kernel products alone on the mixture workload (--n points, --nrhs right-hand sides,
+    --precision form, P.V form from --tc-pv): --warmup untimed then --steps timed with CUDA
+    events; for profiling single kernels on small cases."""
+    import torch
+    from paper_1905_10587_gb300.build import build
+    build()
+    from paper_1905_10587_gb300 import api
+    p = _workload(args.n, 0)
+    X = torch.from_numpy(p.X).cuda()
+    rng = np.random.Generator(np.random.PCG64(7))
+    V = torch.from_numpy(rng.normal(size=(p.n, args.nrhs)).astype(np.float32)).cuda()
+    ctx = api.KRR(precision=args.precision, tc_pv=args.tc_pv)
+    for _ in range(args.warmup):
+        ctx.kmvm(X, X, V, p.sigma, p.beta)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.kmvm(X, X, V, p.sigma, p.beta)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"metric": "kernel product ms", "value": ms, "unit": "ms", "higher_is_better": False,
+                      "n": p.n, "nrhs": args.nrhs, "precision": args.precision, "tc_pv": args.tc_pv,
+                      "pairs_per_s": float(p.n) ** 2 / (ms / 1e3)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -729,9 +782,17 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="kernel product: 0 FP32 tiles, 1 tensor-core tiles (default)")
     ap.add_argument("--workload", default="mixture",
-                    choices=["mixture", "batched", "gradient", "cube", "condition"])
+                    choices=["mixture", "batched", "gradient", "cube", "condition", "product"])
+    ap.add_argument("--nrhs", type=int, default=16, help="product workload: right-hand sides")
+    ap.add_argument("--tc-pv", type=int, default=1, choices=[0, 1, 2],
+                    help="product workload: P.V form (opts.tc_pv)")
     ap.add_argument("--cube-iters", type=int, default=300)
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="split counts from the cost model instead of the tuning table")
+    ap.add_argument("--tune-file", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                        ".krr_tune.json"),
+                    help="JSON tuning table read before and written after tuning")
     ap.add_argument("--grouped", action="store_true",
                     help="batched workload: lockstep solve with one launch per step over all problems")
     args = ap.parse_args()
@@ -739,6 +800,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "product":
+        return run_product(args)
     if args.workload == "gradient":
         return run_gradient(args)
     if args.workload == "cube":

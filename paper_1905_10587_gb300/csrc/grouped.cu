@@ -469,6 +469,31 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
     }
     krr_ctx* ctx = ctxs[0];   // launches of the grouped kernels are accounted to it
     int rc_all = KRR_OK;
+    // fork/join events of the work that runs on the problems' own streams
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join(nprob, nullptr);
+    bool ev_ok = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < nprob && ev_ok; ++i)
+        ev_ok = cudaEventCreateWithFlags(&ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ev_ok) rc_all = KRR_E_CUDA;
+    // problems handed back to their own solve start at once, on a thread of their own
+    std::vector<std::thread> fb_threads;
+    std::vector<char> fb_started(nprob, 0);
+    std::vector<krr_solve_info> fb_info(nprob);
+    std::vector<int> fb_status(nprob, KRR_E_STATE);
+    auto start_fallback = [&](int i) {
+        cudaEventRecord(ev_fork, S);                     // after every grouped step that touched it
+        cudaStreamWaitEvent(streams[i], ev_fork, 0);
+        ctxs[i]->stream = streams[i];
+        fb_started[i] = 1;
+        fb_threads.emplace_back([&, i]() {
+            cudaSetDevice(dev);
+            const krr_problem& p = probs[i];
+            std::memset(&fb_info[i], 0, sizeof(krr_solve_info));
+            fb_status[i] = krr_solve(ctxs[i], p.X, p.Y, nrhs, tol, p.alpha, &fb_info[i]);
+            cudaStreamSynchronize(streams[i]);
+        });
+    };
     {
         GDev gd;
         GPinned gh;
@@ -690,12 +715,22 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
 
         // ---- the product q = (K + beta I) p of every active problem, and p . q partials
         auto product = [&]() -> int {
-            // problems without tensor-core features: their own product launches
+            // problems outside the grouped launch: their own product on their own stream,
+            // forked from S and joined before the first reduction, so that they overlap one
+            // another and the grouped launch
+            std::vector<int> forked;
             for (int ai = 0; ai < n_act; ++ai) {
                 const int i = alist[ai];
                 if (tcp[i]) continue;
+                if (forked.empty()) KRR_TRY_CUDA(cudaEventRecord(ev_fork, S));
                 krr_ctx* c = ctxs[i];
-                KRR_RET(square_product(c, pv + off[i], nrhs, qv + off[i], (o.precision == 1 && c->FA) ? 1 : 0));
+                KRR_TRY_CUDA(cudaStreamWaitEvent(streams[i], ev_fork, 0));
+                c->stream = streams[i];
+                const int prc = square_product(c, pv + off[i], nrhs, qv + off[i], (o.precision == 1 && c->FA) ? 1 : 0);
+                c->stream = S;
+                if (prc != KRR_OK) return prc;
+                KRR_TRY_CUDA(cudaEventRecord(ev_join[i], streams[i]));
+                forked.push_back(i);
             }
             int c0 = 0, ci = 0;
             while (c0 < nrhs) {
@@ -719,6 +754,8 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                     KRR_RET(launch_kmvm_tcpv_table(ctx, d_pv, np, items, ch, d_err));
                 }
                 // the reduction (tensor-core problems) or the p . q partials alone (others)
+                for (int i : forked) KRR_TRY_CUDA(cudaStreamWaitEvent(S, ev_join[i], 0));
+                forked.clear();
                 const int b0 = colstart[c0], nb = colstart[c0 + ch] - b0;
                 if (nb > 0) {
                     k_g_reduce_pq<<<nb, GV_T, 0, S>>>(d_vb, d_gp, c0, ch, ksc, any_tc, pv, qv, d_vpart, b0);
@@ -762,14 +799,19 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
             return KRR_OK;
         };
 
+        // true residuals of the problems in U, each on its own stream (forked from S, joined
+        // back), so that several problems' float-float residuals run at the same time
         auto true_residuals = [&](const std::vector<int>& U) -> int {
+            KRR_TRY_CUDA(cudaEventRecord(ev_fork, S));
             for (int i : U) {
                 krr_ctx* c = ctxs[i];
+                KRR_TRY_CUDA(cudaStreamWaitEvent(streams[i], ev_fork, 0));
+                c->stream = streams[i];
                 const long long tot = probs[i].n * nrhs;
                 double* r64;
                 KRR_RET(bufT(c, "g_r64", (size_t)tot, &r64));   // allocated before the loop
                 KRR_RET(launch_accumulate(c, x + off[i], probs[i].alpha, tot));
-                KRR_TRY_CUDA(cudaMemsetAsync(x + off[i], 0, sizeof(float) * tot, S));
+                KRR_TRY_CUDA(cudaMemsetAsync(x + off[i], 0, sizeof(float) * tot, c->stream));
                 if (o.residual == 1)
                     KRR_RET(launch_residual_hp(c, probs[i].X, probs[i].n, probs[i].d, c->sigma, c->beta,
                                                probs[i].Y, probs[i].alpha, nrhs, r64));
@@ -778,7 +820,10 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                                                probs[i].Y, probs[i].alpha, nrhs, r64));
                 KRR_RET(launch_dot64(c, r64, r64, probs[i].n, nrhs, d_norm + (size_t)i * nrhs));
                 KRR_RET(launch_convert(c, r64, r + off[i], tot));
+                KRR_TRY_CUDA(cudaEventRecord(ev_join[i], streams[i]));
+                c->stream = S;
             }
+            for (int i : U) KRR_TRY_CUDA(cudaStreamWaitEvent(S, ev_join[i], 0));
             KRR_TRY_CUDA(cudaMemcpyAsync(h_norm, d_norm, sizeof(double) * ns, cudaMemcpyDeviceToHost, S));
             KRR_TRY_CUDA(cudaStreamSynchronize(S));
             return KRR_OK;
@@ -953,7 +998,9 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                     if (changed) {
                         // compact the tables to the problems still running (finished ones had
                         // their correction folded by the true residual; abandoned ones are
-                        // solved again from zero below)
+                        // solved again from zero by their own solve, started now)
+                        for (int i = 0; i < nprob; ++i)
+                            if (st[i].fallback && !fb_started[i]) start_fallback(i);
                         std::vector<int> old = alist;
                         std::vector<int> keep_restart;
                         for (int ai = 0; ai < n_act; ++ai)
@@ -986,7 +1033,20 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
         }
         cudaStreamSynchronize(S);
     }
+    for (auto& t : fb_threads) t.join();
+    for (int i = 0; i < nprob; ++i) {
+        if (!fb_started[i]) continue;
+        const int it = info[i].iters, mv = info[i].mvm_count;
+        info[i] = fb_info[i];
+        info[i].iters += it;                 // the grouped iterations count too
+        info[i].mvm_count += mv;
+        info[i].status = fb_status[i];
+        status[i] = fb_status[i];
+    }
     for (int i = 0; i < nprob; ++i) ctxs[i]->stream = streams[i];
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    for (cudaEvent_t e : ev_join)
+        if (e) cudaEventDestroy(e);
     cudaStreamDestroy(S);
     if (rc_all != KRR_OK && rc_all != KRR_E_TIMEOUT) {
         cleanup();
@@ -1002,7 +1062,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
         if (conv)
             for (int c = 0; c < nrhs; ++c)
                 if (!(info[i].rel_residual[c] <= tol)) conv = false;
-        if (!conv && (status[i] == KRR_OK || status[i] == KRR_E_STATE)) todo.push_back(i);
+        if (!conv && !fb_started[i] && (status[i] == KRR_OK || status[i] == KRR_E_STATE)) todo.push_back(i);
     }
     if (!todo.empty()) {
         std::vector<std::thread> pool;
