@@ -112,7 +112,10 @@ typedef struct krr_opts {
                              the tensor-core product its P.V form) from the tuning table
                              where it has an entry for the configuration (krr_autotune,
                              krr_tune_load); 0 (default): from the cost model           */
-    int    reserved[2];
+    int    tc_vfold;      /* 1 (default): the tensor-core product with one right-hand side
+                             folds v into the exponent (2^(t + log2|v_j|), columns taken
+                             in two sign groups), so its epilogue loads no V; 0: FFMA    */
+    int    reserved[1];
     double strong_f;      /* 0 (default): the build selects anchors by pivoted QR (Algorithm 1
                              step 3 as Section 3 remarks); f > 1: by strong RRQR with bound
                              f (Gu-Eisenstat; the factorization Eq. (4) assumes), see

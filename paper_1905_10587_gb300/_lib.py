@@ -28,7 +28,7 @@ class KrrOpts(C.Structure):
                 ("precision", C.c_int), ("residual", C.c_int), ("pivot_tol", C.c_double),
                 ("escalate", C.c_int), ("sparse_r", C.c_int), ("wait_limit_log2", C.c_int),
                 ("test_stall_copies", C.c_int), ("no_precond", C.c_int), ("recurrence", C.c_int),
-                ("strong_swaps", C.c_int), ("ex2_correct", C.c_int), ("tc_pv", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int * 2),
+                ("strong_swaps", C.c_int), ("ex2_correct", C.c_int), ("tc_pv", C.c_int), ("autotune", C.c_int), ("tc_vfold", C.c_int), ("reserved", C.c_int * 1),
                 ("strong_f", C.c_double)]
 
 

@@ -347,6 +347,7 @@ int krr_default_opts(krr_opts* o) {
     o->recurrence = 0;
     o->ex2_correct = 1;
     o->tc_pv = 1;
+    o->tc_vfold = 1;
     return KRR_OK;
 }
 
@@ -368,6 +369,7 @@ int krr_create(krr_ctx** out, const krr_opts* opts, void* stream) {
         ctx->opts.no_precond < 0 || ctx->opts.no_precond > 1 ||
         ctx->opts.ex2_correct < 0 || ctx->opts.ex2_correct > 1 || ctx->opts.tc_pv < 0 ||
         ctx->opts.tc_pv > 2 || ctx->opts.autotune < 0 || ctx->opts.autotune > 1 ||
+        ctx->opts.tc_vfold < 0 || ctx->opts.tc_vfold > 1 ||
         !(ctx->opts.strong_f == 0.0 || ctx->opts.strong_f > 1.0) || ctx->opts.strong_swaps < 0 ||
         !(ctx->opts.anchor_rtol >= 0.0) || !(ctx->opts.pivot_tol >= 0.0) || ctx->opts.pivot_tol >= 1.0) {
         delete ctx;

@@ -332,7 +332,8 @@ __device__ __forceinline__ void split3(float v, __nv_bfloat16& h, __nv_bfloat16&
 
 // Features of point i (packed xh, a at P[i*ps + dk]) written into 128-row tiles in the
 // 128-byte swizzled layout (K slabs of 64): role 0 = row operand, role 1 = column
-// operand.  Rows beyond n and K columns beyond 6 dk + 6 are zero.
+// operand.  The row operand also has ones at K = 6 dk + 6 .. 6 dk + 8 (see the V-folded
+// product).  Rows beyond n and the remaining K columns are zero.
 __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, int ps, int Kp,
                               int role, long long nrows_pad, unsigned char* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,10 +365,96 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
     split3(P[i * ps + dk], a1, a2, a3);
     if (role == 0) {
         put(k++, a1); put(k++, a2); put(k++, a3); put(k++, one); put(k++, one); put(k++, one);
+        // three more ones, against the column operand's log2|v_j| in the V-folded product
+        // (zero in the plain column features, so they add nothing elsewhere)
+        put(k++, one); put(k++, one); put(k++, one);
     } else {
         put(k++, one); put(k++, one); put(k++, one); put(k++, a1); put(k++, a2); put(k++, a3);
     }
     for (; k < Kp; ++k) put(k, zero);
+}
+
+// ------------------------------------------------------------------ V folded into the exponent
+// With one right-hand side v the contraction folds into the exponent:
+//     sum_j 2^t_ij v_j = sum_{v_j >= 0} 2^(t_ij + L_j) - sum_{v_j < 0} 2^(t_ij + L_j),
+//     L_j = log2 |2^e v_j|   (-1000, so that 2^(t + L) = 0, for v_j = 0 and padding columns)
+// with e putting max |2^e v| in [2^14, 2^15).  The column features carry L_j (BF16 x3 at
+// K = 6 dk + 6 .. 6 dk + 8, against the row operand's ones) and the columns are partitioned
+// stably, v >= 0 first: every 32-column chunk but the one at the boundary then adds to a
+// single sum, and the epilogue does one ex2 and one FADD per pair with no V to load.
+constexpr int VF_BLK = 1024;   // columns per block of the partition
+
+// cnt[b] = number of v_j >= 0 in block b
+__global__ void __launch_bounds__(VF_BLK) k_vf_count(const float* __restrict__ V, int n, int* __restrict__ cnt) {
+    __shared__ int wc[VF_BLK / 32];
+    const int j = blockIdx.x * VF_BLK + threadIdx.x;
+    const unsigned m = __ballot_sync(0xffffffffu, j < n && !(V[min(j, n - 1)] < 0.f));
+    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < VF_BLK / 32; ++w) t += wc[w];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// off[b] = exclusive prefix of cnt; *bnd = number of v_j >= 0 (one thread; nblk <= 2^20 / 1024)
+__global__ void k_vf_scan(const int* __restrict__ cnt, int nblk, int* __restrict__ off, int* __restrict__ bnd) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int t = 0;
+    for (int b = 0; b < nblk; ++b) {
+        off[b] = t;
+        t += cnt[b];
+    }
+    *bnd = t;
+}
+
+// Column j's feature row (Kp BF16 in the tiled, swizzled layout) moves to its place in the
+// partition, with L_j written into K = k0 .. k0 + 2; rows n .. ncp - 1 stay in place with
+// L = -1000.
+__global__ void __launch_bounds__(VF_BLK)
+k_vf_scatter(const float* __restrict__ V, int n, int ncp, const int* __restrict__ off, const int* __restrict__ bnd,
+             const int* __restrict__ vexp, const unsigned char* __restrict__ FB, int Kp, int k0,
+             unsigned char* __restrict__ FBv) {
+    __shared__ int wpre[VF_BLK / 32];
+    const int j = blockIdx.x * VF_BLK + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float vj = j < n ? V[j] : 0.f;
+    const bool pos = j < n && !(vj < 0.f);
+    const unsigned m = __ballot_sync(0xffffffffu, pos);
+    if (lane == 0) wpre[w] = __popc(m);
+    __syncthreads();
+    if (j >= ncp) return;
+    int before = 0;                               // v >= 0 columns before j in this block
+    for (int i = 0; i < w; ++i) before += wpre[i];
+    before += __popc(m & ((1u << lane) - 1u));
+    int dst = j;
+    if (j < n) {
+        const int pb = off[blockIdx.x] + before;  // v >= 0 columns before j
+        dst = pos ? pb : *bnd + (j - pb);
+    }
+    float L = -1000.f;
+    if (j < n && vj != 0.f) L = log2f(fabsf(ldexpf(vj, vexp[0])));
+    __nv_bfloat16 h, mm, l;
+    split3(L, h, mm, l);
+    if (L == -1000.f) { h = __float2bfloat16_rn(-1000.f); mm = __float2bfloat16_rn(0.f); l = mm; }
+    const uint32_t tileA = 128u * Kp * 2u;
+    const unsigned char* src = FB + (size_t)(j >> 7) * tileA + (size_t)(j & 127) * 128u;
+    unsigned char* dd = FBv + (size_t)(dst >> 7) * tileA + (size_t)(dst & 127) * 128u;
+    for (int kc = 0; kc < Kp / 8; ++kc) {         // 16-byte chunks of 8 K values
+        const int sl = kc >> 3, c = kc & 7;
+        uint4 x = *reinterpret_cast<const uint4*>(src + sl * 16384 + ((c ^ (j & 7)) << 4));
+        if (kc * 8 + 7 >= k0 && kc * 8 <= k0 + 2) {
+            __nv_bfloat16* e = reinterpret_cast<__nv_bfloat16*>(&x);
+            for (int u = 0; u < 8; ++u) {
+                const int k = kc * 8 + u;
+                if (k == k0) e[u] = h;
+                else if (k == k0 + 1) e[u] = mm;
+                else if (k == k0 + 2) e[u] = l;
+            }
+        }
+        *reinterpret_cast<uint4*>(dd + sl * 16384 + ((c ^ (dst & 7)) << 4)) = x;
+    }
 }
 
 // ------------------------------------------------------------------ product kernel
@@ -384,8 +471,9 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
 //                             8 epilogue warps of the tile's parity, which read V from it)
 //   t_full[b] / t_empty[b]    TMEM accumulator buffer b (2 x 256 columns), read by the
 //                             8 epilogue warps of parity b
-constexpr int TC_EPI_WARPS = 16;
-constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+// EW epilogue warps: 16 (two per tile parity and TMEM lane quarter, 128 columns each); the
+// code also takes 32 (64 columns each), which only fits a CTA without the two issuing warps
+constexpr int tc_threads(int ew) { return 32 * (2 + ew); }
 constexpr int TC_BN = 256;        // columns per tile
 constexpr int TC_ROWS = 128;      // rows per work item
 constexpr int TC_NSMAX = 4;       // most pipeline stages; the count is even, so that a
@@ -401,12 +489,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int NRHS>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// VF: V folded into the exponent (NRHS = 1; FB holds the partitioned, log2|v|-carrying
+// column features, vf_bnd the number of v >= 0 columns and vf_sc = 2^-(15 + e), of which
+// 2^15 vf_sc = 2^-e undoes the scale of v).
+template <int NRHS, int EW, bool VF>
+__global__ void __launch_bounds__(tc_threads(EW), 1)
 k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict__ FB, int Kp,
           int nr, int nc, int ncp, const float* __restrict__ Vp, int items, int splits,
           int tiles_per_split, int ns, double* __restrict__ part, int* __restrict__ err,
-          long long wlimit, int stall_copies) {
+          long long wlimit, int stall_copies, const int* __restrict__ vf_bnd, const double* __restrict__ vf_sc) {
+    static_assert(!VF || NRHS == 1, "the V-folded form takes one right-hand side");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzle atoms need 1024-byte alignment; the launch adds 1 KB of slack for this
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -423,11 +515,12 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         mbar_init(&sh->a_empty, 1);
         for (int s = 0; s < TC_NSMAX; ++s) {
             mbar_init(&sh->s_full[s], 1);
-            mbar_init(&sh->s_empty[s], 1 + TC_EPI_WARPS / 2);   // MMA + the 8 warps of its parity
+            // MMA + the epilogue warps of its parity, which read V from it (not when V is folded)
+            mbar_init(&sh->s_empty[s], VF ? 1 : 1 + EW / 2);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sh->t_full[b], 1);
-            mbar_init(&sh->t_empty[b], TC_EPI_WARPS / 2);
+            mbar_init(&sh->t_empty[b], EW / 2);
         }
         mbar_init(&sh->drain, 1);
         sh->abort = 0;
@@ -466,7 +559,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 for (int t = t0; t < t1; ++t) {
                     const int s = (int)(g % (uint32_t)ns);
                     if (!mbar_wait(&sh->s_empty[s], ((g / ns) & 1u) ^ 1u, wlimit)) { ok = false; break; }
-                    mbar_expect_tx(&sh->s_full[s], tileB + vbytes);
+                    mbar_expect_tx(&sh->s_full[s], tileB + (VF ? 0u : vbytes));
                     // feature tiles 2t and 2t + 1 (128 rows each, slab-major) become one
                     // 256-row tile per 64-wide K slab: slab sl at sl x 32 KB, rows 128.. at +16 KB
                     unsigned char* dB = sB + (size_t)s * tileB;
@@ -476,7 +569,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                                      FB + (size_t)(2 * t + hf) * tileA + (size_t)sl * 16384u, 16384u,
                                      &sh->s_full[s]);
                     float* dV = sV + s * NRHS * TC_BN;
-                    for (int q = 0; q < NRHS; ++q)
+                    for (int q = 0; q < NRHS && !VF; ++q)
                         bulk_g2s(dV + q * TC_BN, Vp + (size_t)q * ncp + (size_t)t * TC_BN, TC_BN * 4u,
                                  &sh->s_full[s]);
                     ++g;
@@ -541,9 +634,13 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
         // its parity only: on each SM sub-partition two warps work on even tiles and two
         // on odd ones, so the TMEM load latency of one pair hides behind the exponentials
         // of the other.
-        const int e = warp - 2;                       // 0..15
+        static_assert(EW == 16 || EW == 32, "16 or 32 epilogue warps");
+        constexpr int NCP = EW / 8;                   // column parts per tile and parity
+        constexpr int CW = TC_BN / NCP;               // columns per warp: 128 or 64
+        const int e = warp - 2;                       // 0 .. EW - 1
         const int quarter = warp & 3;                 // TMEM lanes this warp may read
-        const int chalf = (e >> 2) & 1, par = e >> 3;
+        const int gi = e >> 2;                        // four consecutive warps cover the quarters
+        const int cpart = gi % NCP, par = gi / NCP;
         const int lrow = quarter * 32 + lane;
         uint32_t g = 0;
         for (int item = blockIdx.x; item < items && !*abort; item += gridDim.x) {
@@ -552,6 +649,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             const int t1 = min(t0 + tiles_per_split, ntiles);
             constexpr int NA = NRHS >= 8 ? 1 : 4;    // independent FMA chains per right-hand side
             float acc[NRHS][NA];
+            float accn[NA];                          // V folded: the sum over v < 0 columns
             double acc64[NRHS];                      // tiles folded in FP64 (cancellation)
 #pragma unroll
             for (int q = 0; q < NRHS; ++q) {
@@ -559,19 +657,45 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
 #pragma unroll
                 for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
             }
+#pragma unroll
+            for (int a = 0; a < NA; ++a) accn[a] = 0.f;
+            const int bnd = VF ? *vf_bnd : 0;
             bool ok = true;
             for (int t = t0; t < t1; ++t, ++g) {
                 if ((int)(g & 1u) != par) continue;
                 const int s = (int)(g % (uint32_t)ns), b = par;
                 ok = mbar_wait(&sh->t_full[b], (g >> 1) & 1u, wlimit) &&
-                     mbar_wait(&sh->s_full[s], (g / ns) & 1u, wlimit);
+                     (VF || mbar_wait(&sh->s_full[s], (g / ns) & 1u, wlimit));
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) { if (lane == 0) give_up(); break; }
                 tc_fence_after();
-                const float* v = sV + s * NRHS * TC_BN + chalf * 128;
-                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TC_BN + chalf * 128);
+                const float* v = sV + s * NRHS * TC_BN + cpart * CW;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TC_BN + cpart * CW);
                 // one 32-column chunk of exponents r (columns 32 hh .. 32 hh + 31)
+                auto chunk_vf = [&](const uint32_t (&r)[32], int hh) {
+                    // which sum each column adds to: the chunk lies on one side of the
+                    // partition boundary, except at most one chunk of the whole product
+                    const int c0 = t * TC_BN + cpart * CW + 32 * hh;
+                    if (c0 + 32 <= bnd) {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) acc[0][u % NA] += ex2f(__uint_as_float(r[u]));
+                    } else if (c0 >= bnd) {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) accn[u % NA] += ex2f(__uint_as_float(r[u]));
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) {
+                            const float ev = ex2f(__uint_as_float(r[u]));
+                            if (c0 + u < bnd) acc[0][u % NA] += ev;
+                            else accn[u % NA] += ev;
+                        }
+                    }
+                };
                 auto chunk = [&](const uint32_t (&r)[32], int hh) {
+                    if constexpr (VF) {
+                        chunk_vf(r, hh);
+                        return;
+                    }
 #pragma unroll
                     for (int j4 = 0; j4 < 8; ++j4) {
                         float ev[4];
@@ -593,8 +717,8 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->t_empty[b]);   // TMEM buffer free again
                 };
-                static_assert(TC_BN == 256, "four 32-column chunks per column half");
-                if constexpr (NRHS <= 2) {
+                static_assert(TC_BN == 256, "32-column chunks");
+                if constexpr (NRHS <= 2 && EW == 16) {
                     // two register sets: the load of chunk c + 1 is in flight while chunk c
                     // is exponentiated
                     uint32_t ra[32], rb[32];
@@ -614,16 +738,16 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 } else {
                     // 32 live registers for the exponents
 #pragma unroll 1
-                    for (int hh = 0; hh < 4; ++hh) {
+                    for (int hh = 0; hh < CW / 32; ++hh) {
                         uint32_t r0[32];
                         tmem_ld32(tb + 32 * hh, r0);
                         tmem_wait_ld(r0);
-                        if (hh == 3) release();
+                        if (hh == CW / 32 - 1) release();
                         chunk(r0, hh);
                     }
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&sh->s_empty[s]);   // V of this stage consumed
+                if (!VF && lane == 0) mbar_arrive(&sh->s_empty[s]);   // V of this stage consumed
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q) {
                     float tot = acc[q][0];
@@ -633,13 +757,23 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
 #pragma unroll
                     for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
                 }
+                if constexpr (VF) {
+                    float tn = accn[0];
+#pragma unroll
+                    for (int a = 1; a < NA; ++a) tn += accn[a];
+                    acc64[0] -= (double)tn;
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) accn[a] = 0.f;
+                }
             }
             if (!ok) break;
             const long long row = (long long)rb * TC_ROWS + lrow;
             if (row < nr) {
+                // vf_sc = 2^-(15 + e) undoes both scales of the P.V form; here P is unscaled
+                const double sc = VF ? *vf_sc * 32768.0 : 1.0;
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q)
-                    part[(((size_t)sp * 4 + par * 2 + chalf) * NRHS + q) * nr + row] = acc64[q];
+                    part[(((size_t)sp * (2 * NCP) + par * NCP + cpart) * NRHS + q) * nr + row] = acc64[q] * sc;
             }
         }
     }
@@ -1313,7 +1447,7 @@ size_t tc_feature_bytes(long long n, int d) {
 }
 
 typedef void (*tc_fn)(const unsigned char*, const unsigned char*, int, int, int, int, const float*,
-                      int, int, int, int, double*, int*, long long, int);
+                      int, int, int, int, double*, int*, long long, int, const int*, const double*);
 
 
 // ---- grouped form: the same kernels over the problems of a batch, one launch each
@@ -1491,14 +1625,48 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
             done += chunk;
             continue;
         }
-        tc_fn fn = chunk == 1 ? &k_kmvm_tc<1> : chunk == 2 ? &k_kmvm_tc<2> : chunk == 4 ? &k_kmvm_tc<4>
-                 : chunk == 8 ? &k_kmvm_tc<8> : &k_kmvm_tc<16>;
-        // V padded to whole 256-column tiles, RHS-major (16-byte aligned bulk copies)
-        float* Vp;
-        KRR_RET(bufT(ctx, "tc_vpad", (size_t)chunk * ncp, &Vp));
-        KRR_TRY_CUDA(cudaMemsetAsync(Vp, 0, sizeof(float) * chunk * ncp, ctx->stream));
-        KRR_TRY_CUDA(cudaMemcpy2DAsync(Vp, sizeof(float) * ncp, V + (size_t)done * nc, sizeof(float) * nc,
-                                       sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
+        // 16 epilogue warps (32 would need 34 warps with the producer and the MMA issuer,
+        // above the 32 warps a CTA may have)
+        const int ew = 16;
+        // one right-hand side: V folded into the exponent (opts.tc_vfold)
+        const bool vf = chunk == 1 && !hp && ctx->opts.tc_vfold;
+        tc_fn fn = vf ? &k_kmvm_tc<1, 16, true> : chunk == 1 ? &k_kmvm_tc<1, 16, false>
+                 : chunk == 2 ? &k_kmvm_tc<2, 16, false> : chunk == 4 ? &k_kmvm_tc<4, 16, false>
+                 : chunk == 8 ? &k_kmvm_tc<8, 16, false> : &k_kmvm_tc<16, 16, false>;
+        const int ngroups = ew / 4;                   // partial sums per split: parity x column part
+        // V padded to whole 256-column tiles, RHS-major (16-byte aligned bulk copies), or, with
+        // V folded into the exponent, the partitioned column features that carry log2 |v|
+        float* Vp = nullptr;
+        const unsigned char* FBk = FB;
+        int* vf_bnd = nullptr;
+        double* vf_sc = nullptr;
+        if (vf) {
+            unsigned char* FBv;
+            int *vexp, *cnt, *off;
+            const int nblk = (int)ceil_div(nc, VF_BLK);
+            KRR_RET(bufT(ctx, "vf_fb", (size_t)(ncp / 128) * 128 * Kp * 2, &FBv));
+            KRR_RET(bufT(ctx, "vf_exp", 1, &vexp));
+            KRR_RET(bufT(ctx, "vf_sc", 1, &vf_sc));
+            KRR_RET(bufT(ctx, "vf_cnt", (size_t)nblk, &cnt));
+            KRR_RET(bufT(ctx, "vf_off", (size_t)nblk, &off));
+            KRR_RET(bufT(ctx, "vf_bnd", 1, &vf_bnd));
+            const float* Vc = V + (size_t)done * nc;
+            k_pv_vscale<<<1, 512, 0, ctx->stream>>>(Vc, (int)nc, (int)nc, vexp, vf_sc);
+            KRR_CHECK_LAUNCH();
+            k_vf_count<<<nblk, VF_BLK, 0, ctx->stream>>>(Vc, (int)nc, cnt);
+            KRR_CHECK_LAUNCH();
+            k_vf_scan<<<1, 32, 0, ctx->stream>>>(cnt, nblk, off, vf_bnd);
+            KRR_CHECK_LAUNCH();
+            k_vf_scatter<<<(unsigned)ceil_div(ncp, VF_BLK), VF_BLK, 0, ctx->stream>>>(
+                Vc, (int)nc, ncp, off, vf_bnd, vexp, FB, Kp, 6 * kernel_dim(d) + 6, FBv);
+            KRR_CHECK_LAUNCH();
+            FBk = FBv;
+        } else {
+            KRR_RET(bufT(ctx, "tc_vpad", (size_t)chunk * ncp, &Vp));
+            KRR_TRY_CUDA(cudaMemsetAsync(Vp, 0, sizeof(float) * chunk * ncp, ctx->stream));
+            KRR_TRY_CUDA(cudaMemcpy2DAsync(Vp, sizeof(float) * ncp, V + (size_t)done * nc, sizeof(float) * nc,
+                                           sizeof(float) * nc, chunk, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
         const uint32_t tileA = 128u * Kp * 2u;
         // stages: four where they fit (K = 64), else two
         int optin = 0;
@@ -1530,20 +1698,20 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
         ctx->last_splits = splits;
         const int items = nrb * splits;
         double* part;
-        KRR_RET(bufT(ctx, "tc_part", (size_t)4 * splits * chunk * nr, &part));
+        KRR_RET(bufT(ctx, "tc_part", (size_t)ngroups * splits * chunk * nr, &part));
         const int grid = std::min(items, ctx->num_sms);
         const long long wlimit = ctx->opts.wait_limit_log2 > 0 ? (1LL << ctx->opts.wait_limit_log2)
                                                                : kWaitLimitDefault;
-        fn<<<grid, TC_THREADS, smem_launch, ctx->stream>>>(FA, FB, Kp, (int)nr, (int)nc, ncp, Vp, items,
-                                                           splits, tps, ns, part, err, wlimit,
-                                                           ctx->opts.test_stall_copies);
+        fn<<<grid, tc_threads(ew), smem_launch, ctx->stream>>>(FA, FBk, Kp, (int)nr, (int)nc, ncp, Vp, items,
+                                                               splits, tps, ns, part, err, wlimit,
+                                                               ctx->opts.test_stall_copies, vf_bnd, vf_sc);
         KRR_CHECK_LAUNCH();
-        // four column groups (tile parity x column half) per split: 4 * splits partial sums
+        // column groups (tile parity x column part) per split: ngroups * splits partial sums
         if (hp)
-            KRR_RET(launch_kmvm_reduce64(ctx, part, 4 * splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
+            KRR_RET(launch_kmvm_reduce64(ctx, part, ngroups * splits, (int)nr, chunk, V64 + (size_t)(done / 2) * nr,
                                          (double)beta, Q64 + (size_t)(done / 2) * nr, ex2_bias_scale(ctx)));
         else
-            KRR_RET(launch_kmvm_reduce(ctx, part, 4 * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
+            KRR_RET(launch_kmvm_reduce(ctx, part, ngroups * splits, (int)nr, chunk, V + (size_t)done * nc, (int)nc,
                                        beta, Q + (size_t)done * nr, (int)nr));
         done += chunk;
     }

@@ -22,9 +22,10 @@ def _case(n=3000, d=6, nrhs=2, seed=31):
     return X, V
 
 
-@pytest.mark.parametrize("nrhs", [2, 16])
+@pytest.mark.parametrize("nrhs", [1, 2, 16])
 def test_stalled_tensor_core_product_times_out_and_reports_it(nrhs):
-    # nrhs = 16 runs the product with P.V on the tensor cores (its own kernel and waits)
+    # nrhs = 1 runs the V-folded product, nrhs = 16 the one with P.V on the tensor cores
+    # (each its own kernel and waits)
     from paper_1905_10587_gb300 import _lib
     from paper_1905_10587_gb300.api import KRR, KRRError
     X, V = _case(nrhs=nrhs)
