@@ -1,8 +1,8 @@
 // Grouped batched solves: the PCG recurrences (Algorithm 5 step 3 with the Algorithm 4
 // preconditioner) of many independent problems advance in lockstep, and every step of an
 // iteration is ONE launch over the work items of all active problems:
-//   product      items (problem, 256-row block, column split) of the tensor-core product
-//                with P.V on the tensor cores (tc_kmvm.cu), after one V-split launch
+//   product      items (problem, 128-row block, column split) of the tensor-core product
+//                with P.V on the tensor cores (tc_kmvm.cu, d <= 9), after one V-split launch
 //   vectors      blocks (problem, column, 2048-row chunk) of the concatenated x, r, z, p, q
 //   Woodbury     blocks (problem, 1024-row chunk) of F^T r, threads (problem, column, anchor)
 //                of its reduction, blocks (problem, anchor) of the two triangular products,

@@ -443,7 +443,9 @@ k_vf_scatter(const float* __restrict__ V, int n, int ncp, const int* __restrict_
     unsigned char* dd = FBv + (size_t)(dst >> 7) * tileA + (size_t)(dst & 127) * 128u;
     for (int kc = 0; kc < Kp / 8; ++kc) {         // 16-byte chunks of 8 K values
         const int sl = kc >> 3, c = kc & 7;
-        uint4 x = *reinterpret_cast<const uint4*>(src + sl * 16384 + ((c ^ (j & 7)) << 4));
+        // padding rows (j >= n) get zero features; they may lie past the base features
+        uint4 x = j < n ? *reinterpret_cast<const uint4*>(src + sl * 16384 + ((c ^ (j & 7)) << 4))
+                        : make_uint4(0u, 0u, 0u, 0u);
         if (kc * 8 + 7 >= k0 && kc * 8 <= k0 + 2) {
             __nv_bfloat16* e = reinterpret_cast<__nv_bfloat16*>(&x);
             for (int u = 0; u < 8; ++u) {
@@ -460,11 +462,13 @@ k_vf_scatter(const float* __restrict__ V, int n, int ncp, const int* __restrict_
 // ------------------------------------------------------------------ product kernel
 // Warp-specialised persistent CTA (one per SM): warp 0 lane 0 streams feature tiles
 // with cp.async.bulk, warp 1 lane 0 issues tcgen05.mma, warps 2..17 are the epilogue.
-// A work item is 128 rows (one M = 128 MMA) against a range of 256-column tiles.  Every
-// tcgen05.mma of this kind takes about 194 cycles whatever its N (measured on GB300 for
-// N = 16 .. 256, A in shared or tensor memory, one or several accumulators), so the
-// exponent MMAs run at the widest N, 256: Kp / 16 MMAs per 32768 pairs, which at Kp = 64
-// (d <= 9) is 776 cycles against 1024 cycles of ex2 at 32 per clock.
+// A work item is 128 rows (one M = 128 MMA) against a range of 256-column tiles.  A
+// tcgen05.mma of this kind costs at least ~99 cycles (N <= 64) and ~172 at N = 256
+// (measured on GB300 with one thread issuing back to back), so the exponent MMAs run at
+// the widest N: Kp / 16 MMAs per 32768 pairs, about 690 cycles at Kp = 64 (d <= 9)
+// against 1024 cycles of ex2 at 32 per clock.  What bounds the kernel is the epilogue:
+// a tcgen05.ld of 32 columns takes ~510 cycles to arrive, and tcgen05.wait::ld waits
+// for all of a thread's loads, so each warp has about one load in flight.
 // Hand-offs are mbarrier full/empty pairs only (no block-wide barrier in the loop):
 //   a_full / a_empty          the 128-row operand of the current work item
 //   s_full[s] / s_empty[s]    column tile stage s (empty needs the MMA commit and the
@@ -797,9 +801,9 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
 // 128 + i); their four sums are the output for row i.  Every product of two FP16 values is
 // exact in FP32 and the representation errors are about 2^-22 relative per entry; the
 // scale 2^15 keeps P' in the normal FP16 range down to P = 2^-29.
-// Why transposed: a tcgen05.mma costs about 194 cycles whatever its N (measured), so the
-// contraction wants the fewest instructions: one per 16 columns x 128 rows x (hi + lo)
-// here, against two per 16 columns with P as the M = 128 operand.  The A operand is the
+// Why transposed: a tcgen05.mma costs at least ~99 cycles whatever its N (measured), so
+// the contraction wants few, wide instructions: one of N = 256 per 16 columns x 128 rows
+// x (hi + lo) here, against two of N <= 32 per 16 columns with P as the M = 128 operand.  The A operand is the
 // V tile (2R rows, at least 16); M = 128 reads 128 rows from its address, and the rows
 // past 2R (whatever shared memory follows) only reach D rows that are never read.
 // D accumulates in FP32 over 16 column tiles; warp 0 then folds it into FP64 sums.
