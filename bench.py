@@ -237,10 +237,9 @@ def run_reference(args):
 
 
 # DRAM bytes of one product launch (dram__bytes_read.sum + dram__bytes_write.sum from one
-# ncu capture of the current kernel on this workload): (form, n, d) -> bytes.  For the
-# tensor-core form this equals its algorithmic bytes (both feature sets, 2 n Kp bytes each,
-# plus V); the column features' re-reads are L2 hits.
-MEASURED_TRAFFIC = {(1, 100000, 8): 26_060_000}
+# ncu capture of the current kernel on this workload): (form, n, d) -> bytes.  Entries are
+# removed whenever the kernel changes and re-taken from a capture of the new one.
+MEASURED_TRAFFIC = {}
 
 
 # ------------------------------------------------------------------ roofline of the product
@@ -250,7 +249,8 @@ def roofline(p, kms, kcnt, clocks, precision, sms):
     Per pair (i, j) and right-hand side count r: the FP32 form issues d FFMA for the
     dot product, one FADD for the norms and r FFMA on the FMA pipe plus one ex2 on the
     MUFU; the tensor-core form moves the exponent onto tcgen05 and leaves one ex2 and
-    r FFMA.  Peak pairs/s = min(FMA-pipe rate / FMA ops per pair, MUFU rate), from
+    r FFMA (with one right-hand side v folded into the exponent: one ex2 and one FADD).
+    Peak pairs/s = min(FMA-pipe rate / FMA ops per pair, MUFU rate), from
     the SM count x 128 FP32 lanes (resp. 32 ex2 per SM per clock on GB300) x the
     largest SM clock seen.
     """
@@ -262,8 +262,9 @@ def roofline(p, kms, kcnt, clocks, precision, sms):
     peak_pairs = min(ffma_rate / fma_per_pair, mufu_rate)
     avg_s = (kms / max(kcnt, 1)) / 1e3
     achieved = (float(p.n) * p.n / avg_s) if kcnt else None
-    name = ("k_kmvm_tc (tcgen05 BF16x3 exponent GEMM + ex2 + FFMA), (K + beta I) p" if precision == 1
-            else "k_kmvm (tiled FP32 kernel product), (K + beta I) p")
+    name = ("k_kmvm_tc<1, 16, true> (tcgen05 BF16x3 exponent GEMM with v folded into the exponent, "
+            "ex2 + FADD), (K + beta I) p; the timed phase includes the v partition and the reduction"
+            if precision == 1 else "k_kmvm (tiled FP32 kernel product), (K + beta I) p")
     return {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
             "peak": peak_pairs / 1e9, "unit": "Gpair/s",
             "frac": (achieved / peak_pairs) if achieved else None,
