@@ -86,7 +86,8 @@ def test_roofline_fields_and_arithmetic():
     assert r["peak"] == pytest.approx(mufu)
     assert r["achieved"] == pytest.approx(1e10 / 1.62e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.MEASURED_TRAFFIC[(1, 100000, 8)]
+    # the ncu DRAM bytes of the current kernel, or None until they have been captured
+    assert r["traffic"] == bench.MEASURED_TRAFFIC.get((1, 100000, 8))
     r0 = bench.roofline(P, kms=3780.0, kcnt=1000, clocks=clocks, precision=0, sms=152)
     assert r0["peak"] == pytest.approx(152 * 128 * 2070e6 / 10 / 1e9)   # d + 1 + nrhs FMA ops
     assert r0["traffic"] is None                                        # not captured for this form
