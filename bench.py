@@ -238,8 +238,10 @@ def run_reference(args):
 
 # DRAM bytes of one product launch (dram__bytes_read.sum + dram__bytes_write.sum from one
 # ncu capture of the current kernel on this workload): (form, n, d) -> bytes.  Entries are
-# removed whenever the kernel changes and re-taken from a capture of the new one.
-MEASURED_TRAFFIC = {}
+# removed whenever the kernel changes and re-taken from a capture of the new one.  The
+# V-folded tensor-core product reads both 64-wide BF16 feature sets (2 x 12.8 MB at n = 10^5)
+# once from DRAM; the column features' re-reads are L2 hits.
+MEASURED_TRAFFIC = {(1, 100000, 8): 25_678_720}
 
 
 # ------------------------------------------------------------------ roofline of the product

@@ -11,9 +11,11 @@
 // Every problem keeps its own CG scalars, column activity and convergence state.  The host
 // reads every problem's recursive residuals once per iteration, runs the true-residual
 // replacements (float-float, per problem) of the problems that call for one, and removes
-// finished problems from the work tables.  A problem whose recurrence breaks down, stalls
-// or keeps showing gaps is finished afterwards by its own krr_solve (which escalates the
-// product form), so the grouped path never returns a worse answer than the one-by-one path.
+// finished problems from the work tables.  A problem whose expansion-form recurrence breaks
+// down, stalls or keeps showing gaps escalates in place to the exact-difference product (run
+// on its own stream), as krr_solve does; one that fails in that form or reaches a limit is
+// finished by its own krr_solve, so the grouped path ends every problem as the one-by-one
+// path would.
 #include "internal.cuh"
 
 #include <algorithm>
@@ -387,7 +389,7 @@ struct GPinned {
 
 // per-problem host state of the grouped recurrence
 struct GState {
-    bool active = false, done = false, fallback = false;
+    bool active = false, done = false, fallback = false, esc_pending = false;
     int it = 0, since = 0, sweeps = 0, restarts = 0, gapped = 0, window = 500, it_best = 0;
     double best = 1.0;
     std::vector<double> yn, rtrue, rec;
@@ -527,6 +529,11 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
         const int chunk_max = nrhs >= 16 ? 16 : nrhs >= 8 ? 8 : nrhs >= 4 ? 4 : nrhs >= 2 ? 2 : 1;
         const int vtile = pv_tile_bytes(chunk_max);
         std::vector<int> tcp(nprob, 0);
+        // product form per problem: the requested one (1 needs tensor-core features, else 0),
+        // and 2 (exact differences) after an escalation
+        std::vector<int> form(nprob, 0);
+        for (int i = 0; i < nprob; ++i)
+            form[i] = o.precision == 1 ? (ctxs[i]->FA ? 1 : 0) : o.precision;
         for (int i = 0; i < nprob; ++i) {
             const krr_ctx* c = ctxs[i];
             const long long n = probs[i].n;
@@ -726,7 +733,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                 krr_ctx* c = ctxs[i];
                 KRR_TRY_CUDA(cudaStreamWaitEvent(streams[i], ev_fork, 0));
                 c->stream = streams[i];
-                const int prc = square_product(c, pv + off[i], nrhs, qv + off[i], (o.precision == 1 && c->FA) ? 1 : 0);
+                const int prc = square_product(c, pv + off[i], nrhs, qv + off[i], form[i]);
                 c->stream = S;
                 if (prc != KRR_OK) return prc;
                 KRR_TRY_CUDA(cudaEventRecord(ev_join[i], streams[i]));
@@ -907,10 +914,19 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                         s.it++;
                         s.since++;
                         info[i].mvm_count++;
-                        if (h_bad[ai]) {           // breakdown: finished by its own solve
-                            s.fallback = true;
-                            s.active = false;
-                            changed = true;
+                        if (h_bad[ai]) {
+                            if (o.escalate && form[i] != 2) {
+                                // non-positive curvature in an expansion form: the correction
+                                // since the last true residual is unverified and is dropped;
+                                // the problem goes on from its verified alpha in form 2
+                                s.esc_pending = true;
+                                KRR_TRY_CUDA(cudaMemsetAsync(x + off[i], 0, sizeof(float) * probs[i].n * nrhs, S));
+                                U.push_back(i);
+                            } else {              // finished by its own solve
+                                s.fallback = true;
+                                s.active = false;
+                                changed = true;
+                            }
                             continue;
                         }
                         const bool last = s.it >= o.max_iter;
@@ -961,6 +977,18 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                                 changed = true;
                                 continue;
                             }
+                            if (s.esc_pending) {          // the breakdown's escalation
+                                s.esc_pending = false;
+                                form[i] = 2;
+                                tcp[i] = 0;
+                                s.gapped = 0;
+                                s.best = worst;
+                                s.it_best = s.it;
+                                s.restarts++;
+                                h_restart[ai] = 1;
+                                changed = true;
+                                continue;
+                            }
                             if (s.it >= o.max_iter || s.sweeps >= o.refine_max) {
                                 s.fallback = true;
                                 s.active = false;
@@ -976,11 +1004,17 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
                                 s.it_best = s.it;
                             }
                             const bool stalled = s.it - s.it_best > s.window;
-                            if (o.escalate && (s.gapped >= 2 || stalled)) {
-                                // the product form, not the recurrence, limits this problem:
-                                // its own solve takes it on with the exact-difference form
-                                s.fallback = true;
-                                s.active = false;
+                            if (o.escalate && form[i] != 2 && (s.gapped >= 2 || stalled)) {
+                                // the product form, not the recurrence, limits this problem: it
+                                // goes on from the replaced residual in the exact-difference form
+                                // (its product then runs on its own stream)
+                                form[i] = 2;
+                                tcp[i] = 0;
+                                s.gapped = 0;
+                                s.best = worst;
+                                s.it_best = s.it;
+                                s.restarts++;
+                                h_restart[ai] = 1;
                                 changed = true;
                                 continue;
                             }
@@ -1028,7 +1062,7 @@ extern "C" int krr_batch_solve_grouped(const krr_problem* probs, int nprob, int 
             info[i].k_eff = ctxs[i]->k_eff;
             info[i].build_ms = ctxs[i]->build_ms;
             info[i].solve_ms = solve_ms;
-            info[i].product_form = (o.precision == 1 && ctxs[i]->FA) ? 1 : 0;
+            info[i].product_form = form[i];
             if (st[i].done) status[i] = KRR_OK;
         }
         cudaStreamSynchronize(S);

@@ -384,22 +384,40 @@ __global__ void k_tc_features(const float* __restrict__ P, long long n, int dk, 
 // single sum, and the epilogue does one ex2 and one FADD per pair with no V to load.
 constexpr int VF_BLK = 1024;   // columns per block of the partition
 
-// cnt[b] = number of v_j >= 0 in block b
-__global__ void __launch_bounds__(VF_BLK) k_vf_count(const float* __restrict__ V, int n, int* __restrict__ cnt) {
+// cnt[b] = number of v_j >= 0 in block b; *vmax = max |v_j| as float bits (non-negative
+// floats order like their bits, so atomicMax on the bits is exact; *vmax starts at 0)
+__global__ void __launch_bounds__(VF_BLK) k_vf_count(const float* __restrict__ V, int n, int* __restrict__ cnt,
+                                                      unsigned* __restrict__ vmax) {
     __shared__ int wc[VF_BLK / 32];
+    __shared__ unsigned wm[VF_BLK / 32];
     const int j = blockIdx.x * VF_BLK + threadIdx.x;
-    const unsigned m = __ballot_sync(0xffffffffu, j < n && !(V[min(j, n - 1)] < 0.f));
-    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(m);
+    const float v = j < n ? V[j] : 0.f;
+    const unsigned m = __ballot_sync(0xffffffffu, j < n && !(v < 0.f));
+    unsigned b = __float_as_uint(fabsf(v));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if ((threadIdx.x & 31) == 0) {
+        wc[threadIdx.x >> 5] = __popc(m);
+        wm[threadIdx.x >> 5] = b;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int t = 0;
-        for (int w = 0; w < VF_BLK / 32; ++w) t += wc[w];
+        unsigned mb = 0;
+        for (int w = 0; w < VF_BLK / 32; ++w) {
+            t += wc[w];
+            mb = max(mb, wm[w]);
+        }
         cnt[blockIdx.x] = t;
+        atomicMax(vmax, mb);
     }
 }
 
-// off[b] = exclusive prefix of cnt; *bnd = number of v_j >= 0 (one thread; nblk <= 2^20 / 1024)
-__global__ void k_vf_scan(const int* __restrict__ cnt, int nblk, int* __restrict__ off, int* __restrict__ bnd) {
+// off[b] = exclusive prefix of cnt; *bnd = number of v_j >= 0; e = 15 - (binary exponent of
+// max |v|) (0 when v is zero or not finite), vexp = e, vsc = 2^-(15 + e) (one thread;
+// nblk <= 2^20 / 1024)
+__global__ void k_vf_scan(const int* __restrict__ cnt, int nblk, int* __restrict__ off, int* __restrict__ bnd,
+                          const unsigned* __restrict__ vmax, int* __restrict__ vexp, double* __restrict__ vsc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int t = 0;
     for (int b = 0; b < nblk; ++b) {
@@ -407,6 +425,13 @@ __global__ void k_vf_scan(const int* __restrict__ cnt, int nblk, int* __restrict
         t += cnt[b];
     }
     *bnd = t;
+    const float m = __uint_as_float(*vmax);
+    int ex = 0;
+    const bool ok = m > 0.f && m <= 3.4028234663852886e38f;
+    if (ok) frexpf(m, &ex);
+    const int e = ok ? 15 - ex : 0;
+    *vexp = e;
+    *vsc = ldexp(1.0, -(15 + e));
 }
 
 // Column j's feature row (Kp BF16 in the tiled, swizzled layout) moves to its place in the
@@ -1654,12 +1679,13 @@ int launch_kmvm_tc(krr_ctx* ctx, const unsigned char* FA, long long nr, const un
             KRR_RET(bufT(ctx, "vf_cnt", (size_t)nblk, &cnt));
             KRR_RET(bufT(ctx, "vf_off", (size_t)nblk, &off));
             KRR_RET(bufT(ctx, "vf_bnd", 1, &vf_bnd));
+            unsigned* vmax;
+            KRR_RET(bufT(ctx, "vf_max", 1, &vmax));
             const float* Vc = V + (size_t)done * nc;
-            k_pv_vscale<<<1, 512, 0, ctx->stream>>>(Vc, (int)nc, (int)nc, vexp, vf_sc);
+            KRR_TRY_CUDA(cudaMemsetAsync(vmax, 0, sizeof(unsigned), ctx->stream));
+            k_vf_count<<<nblk, VF_BLK, 0, ctx->stream>>>(Vc, (int)nc, cnt, vmax);
             KRR_CHECK_LAUNCH();
-            k_vf_count<<<nblk, VF_BLK, 0, ctx->stream>>>(Vc, (int)nc, cnt);
-            KRR_CHECK_LAUNCH();
-            k_vf_scan<<<1, 32, 0, ctx->stream>>>(cnt, nblk, off, vf_bnd);
+            k_vf_scan<<<1, 32, 0, ctx->stream>>>(cnt, nblk, off, vf_bnd, vmax, vexp, vf_sc);
             KRR_CHECK_LAUNCH();
             k_vf_scatter<<<(unsigned)ceil_div(ncp, VF_BLK), VF_BLK, 0, ctx->stream>>>(
                 Vc, (int)nc, ncp, off, vf_bnd, vexp, FB, Kp, 6 * kernel_dim(d) + 6, FBv);

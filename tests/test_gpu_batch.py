@@ -103,10 +103,10 @@ def test_grouped_matches_one_by_one_on_larger_batch():
         assert d <= 1e-3, (p.name, d)
 
 
-def test_grouped_hands_a_breakdown_to_its_own_solve():
+def test_grouped_escalates_a_breakdown_in_place():
     # tight clusters spread over a wide box make the FP32 expansion indefinite: the grouped
-    # recurrence of that problem breaks down, and its own solve (which escalates to the
-    # exact-difference form) finishes it; the other problem converges in the group
+    # recurrence of that problem breaks down, drops its unverified correction and goes on in
+    # the exact-difference form inside the group; the other problem converges beside it
     from paper_1905_10587_gb300 import api
     rng = np.random.Generator(np.random.PCG64(5))
     centres = rng.uniform(0.0, 150.0, size=(40, 3))
