@@ -156,6 +156,30 @@ __device__ __forceinline__ float ex2f(float x) {
     return y;
 }
 
+// Float-float accumulation: (hi, lo) += x with Knuth's TwoSum, an error-free transformation
+// (hi + x = s + e exactly), so hi + lo carries the running sum to about 2^-44 relative per
+// addition.  Six FP32 adds on the FMA pipe, where an FP64 add (after a conversion) takes
+// the FP64 unit, which runs at a small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float z = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(x, z));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+// A running sum of FP32 tile sums: float-float (above), or FP64 where a kernel has no
+// registers to spare for the TwoSum temporaries.
+struct FoldFF {
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(float x) { ff_add(h, l, x); }
+    __device__ __forceinline__ double get() const { return (double)h + (double)l; }
+};
+struct Fold64 {
+    double s = 0.0;
+    __device__ __forceinline__ void add(float x) { s += (double)x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
 // 2^t on the FMA pipe, for the accurate product form: t = m + f with m = round(t)
 // (rounded by adding and subtracting 1.5 * 2^23), |f| <= 1/2 exact, and
 // 2^f = e^(f ln 2) = sum_k (ln 2)^k f^k / k! truncated after k = 7 (the first dropped

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 namespace krr {
 
@@ -133,7 +134,10 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
     float xi[R][D];
     float ai[R];
     float acc[R][NRHS];     // one column tile, FP32
-    double acc64[R][NRHS];  // tiles folded in FP64: smooth kernels cancel heavily across tiles
+    // tiles folded float-float (FP64 for the widest rows, short of registers): smooth
+    // kernels cancel heavily across tiles
+    using Fold = std::conditional_t<(D <= 32), FoldFF, Fold64>;
+    Fold fold[R][NRHS];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const long long i = row0 + r * KM_THREADS + tid;
@@ -142,7 +146,7 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
         for (int c = 0; c < D; ++c) xi[r][c] = ok ? (RAW ? 1.f : 2.f) * Pr[i * PS + c] : 0.f;
         ai[r] = (ok && !RAW) ? Pr[i * PS + D] : 0.f;
 #pragma unroll
-        for (int q = 0; q < NRHS; ++q) acc[r][q] = 0.f, acc64[r][q] = 0.0;
+        for (int q = 0; q < NRHS; ++q) acc[r][q] = 0.f;
     }
 
     const int ntiles = (nc + KM_BN - 1) / KM_BN;
@@ -212,7 +216,7 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int q = 0; q < NRHS; ++q) acc64[r][q] += (double)acc[r][q], acc[r][q] = 0.f;
+            for (int q = 0; q < NRHS; ++q) fold[r][q].add(acc[r][q]), acc[r][q] = 0.f;
     }
 
 #pragma unroll
@@ -223,12 +227,12 @@ k_kmvm(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc, int n
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
                 Q[(size_t)q * ldq + i] =
-                    (float)(acc64[r][q] * (1.0 + (double)kcorr) +
+                    (float)(fold[r][q].get() * (1.0 + (double)kcorr) +
                             (beta != 0.f ? (double)beta * V[(size_t)q * ldv + i] : 0.0));
         } else {
 #pragma unroll
             for (int q = 0; q < NRHS; ++q)
-                part[((size_t)blockIdx.y * NRHS + q) * nr + i] = acc64[r][q];
+                part[((size_t)blockIdx.y * NRHS + q) * nr + i] = fold[r][q].get();
         }
     }
 }
@@ -676,7 +680,7 @@ k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc
     const int tid = threadIdx.x;
     const long long row0 = (long long)blockIdx.x * (KM_THREADS * R);
     float xi[R][D], ai[R], acc[R];
-    double acc64[R];
+    float ah[R], al[R];   // tiles folded float-float
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const long long i = row0 + r * KM_THREADS + tid;
@@ -685,7 +689,7 @@ k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc
         for (int c = 0; c < D; ++c) xi[r][c] = ok ? 2.f * Pr[i * PS + c] : 0.f;
         ai[r] = ok ? Pr[i * PS + D] : 0.f;
         acc[r] = 0.f;
-        acc64[r] = 0.0;
+        ah[r] = al[r] = 0.f;
     }
     const int ntiles = (nc + KM_BN - 1) / KM_BN;
     const int t0 = blockIdx.y * tiles_per_split;
@@ -722,13 +726,13 @@ k_kmvm_dsigma(const float* __restrict__ Pr, int nr, const float* __restrict__ Pc
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc64[r] += (double)acc[r], acc[r] = 0.f;
+        for (int r = 0; r < R; ++r) ff_add(ah[r], al[r], acc[r]), acc[r] = 0.f;
     }
     const double scale = -2.0 * 0.6931471805599453;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const long long i = row0 + r * KM_THREADS + tid;
-        if (i < nr) part[(size_t)blockIdx.y * nr + i] = scale * acc64[r];
+        if (i < nr) part[(size_t)blockIdx.y * nr + i] = scale * ((double)ah[r] + (double)al[r]);
     }
 }
 

@@ -679,10 +679,11 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
             constexpr int NA = NRHS >= 8 ? 1 : 4;    // independent FMA chains per right-hand side
             float acc[NRHS][NA];
             float accn[NA];                          // V folded: the sum over v < 0 columns
-            double acc64[NRHS];                      // tiles folded in FP64 (cancellation)
+            float ah[NRHS], al[NRHS];               // tiles folded float-float (cancellation)
+            float nh = 0.f, nl = 0.f;                // V folded: the v < 0 sum
 #pragma unroll
             for (int q = 0; q < NRHS; ++q) {
-                acc64[q] = 0.0;
+                ah[q] = al[q] = 0.f;
 #pragma unroll
                 for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
             }
@@ -782,7 +783,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                     float tot = acc[q][0];
 #pragma unroll
                     for (int a = 1; a < NA; ++a) tot += acc[q][a];
-                    acc64[q] += (double)tot;
+                    ff_add(ah[q], al[q], tot);
 #pragma unroll
                     for (int a = 0; a < NA; ++a) acc[q][a] = 0.f;
                 }
@@ -790,7 +791,7 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                     float tn = accn[0];
 #pragma unroll
                     for (int a = 1; a < NA; ++a) tn += accn[a];
-                    acc64[0] -= (double)tn;
+                    ff_add(nh, nl, tn);
 #pragma unroll
                     for (int a = 0; a < NA; ++a) accn[a] = 0.f;
                 }
@@ -802,7 +803,8 @@ k_kmvm_tc(const unsigned char* __restrict__ FA, const unsigned char* __restrict_
                 const double sc = VF ? *vf_sc * 32768.0 : 1.0;
 #pragma unroll
                 for (int q = 0; q < NRHS; ++q)
-                    part[(((size_t)sp * (2 * NCP) + par * NCP + cpart) * NRHS + q) * nr + row] = acc64[q] * sc;
+                    part[(((size_t)sp * (2 * NCP) + par * NCP + cpart) * NRHS + q) * nr + row] =
+                        ((double)ah[q] + (double)al[q] - (VF ? (double)nh + (double)nl : 0.0)) * sc;
             }
         }
     }
