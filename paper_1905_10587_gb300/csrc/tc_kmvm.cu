@@ -7,11 +7,13 @@
 //     row i    : [2h, 2h, 2m, 2h, 2m, 2l]_c ... , a1, a2, a3, 1, 1, 1
 //     column j : [ H,  M,  H,  L,  M,  H]_c ... ,  1,  1,  1, A1, A2, A3
 // (the products hH + hM + mH + hL + mM + lH keep every term above 2^-24 relative).
-// A CTA owns 256 rows (two M = 128 MMAs) and streams 128-column tiles: features
-// arrive by cp.async.bulk on an mbarrier, tcgen05.mma accumulates t into TMEM
-// (two 256-column buffers, so the MMA of tile t+1 overlaps the epilogue of tile t),
-// and the epilogue reads TMEM with tcgen05.ld and does one ex2 (MUFU) and one FFMA
-// per pair and right-hand side.  Every wait is bounded; on timeout the kernel sets
+// A work item is 128 rows (one M = 128 MMA) against a range of 256-column tiles:
+// features arrive by cp.async.bulk on an mbarrier, tcgen05.mma accumulates t into
+// TMEM (two 256-column buffers, so the MMA of tile t+1 overlaps the epilogue of tile
+// t), and the epilogue reads TMEM with tcgen05.ld and does one ex2 (MUFU) per pair and
+// one FFMA per pair and right-hand side, or, with one right-hand side folded into the
+// exponent, one add.  With many right-hand sides the contraction runs as a second
+// tcgen05 MMA (k_kmvm_tcpv below).  Every wait is bounded; on timeout the kernel sets
 // an error word, stops issuing work, frees its TMEM and returns.
 #include "internal.cuh"
 
@@ -491,9 +493,13 @@ k_vf_scatter(const float* __restrict__ V, int n, int ncp, const int* __restrict_
 // tcgen05.mma of this kind costs at least ~99 cycles (N <= 64) and ~172 at N = 256
 // (measured on GB300 with one thread issuing back to back), so the exponent MMAs run at
 // the widest N: Kp / 16 MMAs per 32768 pairs, about 690 cycles at Kp = 64 (d <= 9)
-// against 1024 cycles of ex2 at 32 per clock.  What bounds the kernel is the epilogue:
-// a tcgen05.ld of 32 columns takes ~510 cycles to arrive, and tcgen05.wait::ld waits
-// for all of a thread's loads, so each warp has about one load in flight.
+// against 1024 cycles of ex2 at 32 per clock.  Measured per role with clock64 on the
+// mixture (n = 10^5, v folded), an epilogue warp spends ~60% of its time on the
+// exponentials, ~12% waiting for the MMA, and under 2% waiting for TMEM loads (each
+// lands behind the previous chunk); a tile takes ~1500 cycles, ~66% of the MUFU rate,
+// against ~88% for a free-running stream of 32-column loads, ex2 and adds.  The rest is
+// the per-tile hand-off chain (MMA commit, TMEM release, a tile's first load): with a
+// quarter of the MMAs, no exponentials or half the loads the tile is 2-11% shorter.
 // Hand-offs are mbarrier full/empty pairs only (no block-wide barrier in the loop):
 //   a_full / a_empty          the 128-row operand of the current work item
 //   s_full[s] / s_empty[s]    column tile stage s (empty needs the MMA commit and the
